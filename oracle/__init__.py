@@ -1,0 +1,248 @@
+"""Python handle on the CPU oracle (oracle/ldpc_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+CPU-baseline leg of the benchmark.  The CUDA library never uses it.
+
+Each wrapper takes and returns numpy arrays; the C code is built on first
+use (gcc, -O2 -ffp-contract=off) next to this file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ldpc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libldpc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library; returns its path."""
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(
+                 os.path.join(_HERE, "ldpc_oracle.h")))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math",
+               "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True, cwd=_HERE)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("alpha", ctypes.c_float),
+                ("normalise", ctypes.c_int), ("early_stop", ctypes.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, i32, i64, u64, f32 = (ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_int64, ctypes.c_uint64,
+                                      ctypes.c_float)
+            L.ldpc_ref_code_create.argtypes = [vp, i32, i32, i32, i32,
+                                               ctypes.POINTER(vp)]
+            L.ldpc_ref_code_destroy.argtypes = [vp]
+            L.ldpc_ref_code_destroy.restype = None
+            L.ldpc_ref_code_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 7
+            L.ldpc_ref_row_vars.argtypes = [vp, i32, vp, i32]
+            L.ldpc_ref_encode.argtypes = [vp, vp, vp, i64]
+            L.ldpc_ref_syndrome_weight.argtypes = [vp, vp]
+            L.ldpc_ref_philox4x32_10.argtypes = [vp, vp, vp]
+            L.ldpc_ref_philox4x32_10.restype = None
+            L.ldpc_ref_gen_info.argtypes = [u64, i64, i64, i32, vp]
+            L.ldpc_ref_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32,
+                                              ctypes.POINTER(f32),
+                                              ctypes.POINTER(f32)]
+            L.ldpc_ref_box_muller.restype = None
+            L.ldpc_ref_lnf.argtypes = [f32]
+            L.ldpc_ref_lnf.restype = f32
+            L.ldpc_ref_sincos_turn.argtypes = [ctypes.c_uint32,
+                                               ctypes.POINTER(f32),
+                                               ctypes.POINTER(f32)]
+            L.ldpc_ref_sincos_turn.restype = None
+            L.ldpc_ref_awgn_llr.argtypes = [vp, i64, i64, i32, u64, f32, f32, vp]
+            L.ldpc_ref_quantize_i8.argtypes = [vp, vp, i64, f32, i32]
+            for name in ("ldpc_ref_decode_layered_f32",
+                         "ldpc_ref_decode_flooding_f32"):
+                getattr(L, name).argtypes = [vp, vp, i64,
+                                             ctypes.POINTER(_Params), vp, vp, vp]
+            L.ldpc_ref_decode_layered_i8.argtypes = [
+                vp, vp, i64, ctypes.POINTER(_Params), vp, vp, vp,
+                ctypes.POINTER(i64)]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise OracleError(f"{what} failed with status {status}")
+
+
+class RefCode:
+    """Oracle view of a code: the explicit sparse H built from H_bm."""
+
+    def __init__(self, hbm: np.ndarray, z: int, require_encodable: bool = True):
+        hbm = np.ascontiguousarray(hbm, dtype=np.int16)
+        self.hbm = hbm
+        self._h = ctypes.c_void_p()
+        st = lib().ldpc_ref_code_create(_ptr(hbm), hbm.shape[0], hbm.shape[1],
+                                        int(z), int(require_encodable),
+                                        ctypes.byref(self._h))
+        _check(st, "ldpc_ref_code_create")
+        vals = [ctypes.c_int() for _ in range(7)]
+        lib().ldpc_ref_code_info(self._h, *[ctypes.byref(v) for v in vals])
+        (self.n, self.k, self.m, self.z, self.max_row_deg, self.y,
+         self.encodable) = [v.value for v in vals]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.ldpc_ref_code_destroy(h)
+            self._h = None
+
+    @property
+    def nwords(self) -> int:
+        return (self.n + 31) // 32
+
+    def row_vars(self, row: int) -> np.ndarray:
+        buf = np.zeros(64, dtype=np.int32)
+        d = lib().ldpc_ref_row_vars(self._h, row, _ptr(buf), 64)
+        return buf[:d].copy()
+
+    def encode(self, info: np.ndarray) -> np.ndarray:
+        info = np.ascontiguousarray(info, dtype=np.uint8).reshape(-1, self.k)
+        out = np.zeros((info.shape[0], self.n), dtype=np.uint8)
+        _check(lib().ldpc_ref_encode(self._h, _ptr(info), _ptr(out),
+                                     info.shape[0]), "ldpc_ref_encode")
+        return out
+
+    def syndrome_weight(self, bits: np.ndarray) -> int:
+        bits = np.ascontiguousarray(bits, dtype=np.uint8).reshape(self.n)
+        return int(lib().ldpc_ref_syndrome_weight(self._h, _ptr(bits)))
+
+    def _decode(self, fn, llr, dtype, max_iters, alpha, normalise, early_stop,
+                want_post, post_dtype):
+        llr = np.ascontiguousarray(llr, dtype=dtype).reshape(-1, self.n)
+        F = llr.shape[0]
+        hard = np.zeros((F, self.nwords), dtype=np.uint32)
+        iters = np.zeros(F, dtype=np.int32)
+        post = np.zeros((F, self.n), dtype=post_dtype) if want_post else None
+        p = _Params(int(max_iters), float(alpha), int(normalise), int(early_stop))
+        return llr, F, hard, iters, post, p
+
+    def decode_layered_f32(self, llr, max_iters=10, alpha=0.75, normalise=True,
+                           early_stop=False, want_post=True):
+        llr, F, hard, iters, post, p = self._decode(
+            None, llr, np.float32, max_iters, alpha, normalise, early_stop,
+            want_post, np.float32)
+        _check(lib().ldpc_ref_decode_layered_f32(
+            self._h, _ptr(llr), F, ctypes.byref(p), _ptr(hard), _ptr(iters),
+            _ptr(post)), "ldpc_ref_decode_layered_f32")
+        return hard, iters, post
+
+    def decode_flooding_f32(self, llr, max_iters=10, alpha=0.75, normalise=True,
+                            early_stop=False, want_post=True):
+        llr, F, hard, iters, post, p = self._decode(
+            None, llr, np.float32, max_iters, alpha, normalise, early_stop,
+            want_post, np.float32)
+        _check(lib().ldpc_ref_decode_flooding_f32(
+            self._h, _ptr(llr), F, ctypes.byref(p), _ptr(hard), _ptr(iters),
+            _ptr(post)), "ldpc_ref_decode_flooding_f32")
+        return hard, iters, post
+
+    def decode_layered_i8(self, llr_q, max_iters=10, normalise=True,
+                          early_stop=False, want_post=True
+                          ) -> Tuple[np.ndarray, np.ndarray, np.ndarray, int]:
+        llr, F, hard, iters, post, p = self._decode(
+            None, llr_q, np.int8, max_iters, 0.75, normalise, early_stop,
+            want_post, np.int8)
+        ev = ctypes.c_int64(0)
+        _check(lib().ldpc_ref_decode_layered_i8(
+            self._h, _ptr(llr), F, ctypes.byref(p), _ptr(hard), _ptr(iters),
+            _ptr(post), ctypes.byref(ev)), "ldpc_ref_decode_layered_i8")
+        return hard, iters, post, int(ev.value)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().ldpc_ref_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def gen_info(seed: int, frame0: int, frames: int, k: int) -> np.ndarray:
+    out = np.zeros((frames, k), dtype=np.uint8)
+    _check(lib().ldpc_ref_gen_info(seed, frame0, frames, k, _ptr(out)),
+           "ldpc_ref_gen_info")
+    return out
+
+
+def lnf(u: float) -> float:
+    return float(lib().ldpc_ref_lnf(u))
+
+
+def sincos_turn(k24: int) -> Tuple[float, float]:
+    s, c = ctypes.c_float(), ctypes.c_float()
+    lib().ldpc_ref_sincos_turn(k24, ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def box_muller(w0: int, w1: int) -> Tuple[float, float]:
+    a, b = ctypes.c_float(), ctypes.c_float()
+    lib().ldpc_ref_box_muller(w0, w1, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def awgn_llr(cw: np.ndarray, frame0: int, seed: int, sigma: float,
+             llr_scale: Optional[float] = None) -> np.ndarray:
+    """eq. (16)-(17) with the Philox noise stream; llr_scale defaults to the
+    float32 value of 2 / sigma^2."""
+    cw = np.ascontiguousarray(cw, dtype=np.uint8)
+    F, n = cw.shape
+    sig = np.float32(sigma)
+    if llr_scale is None:
+        llr_scale = float(np.float32(2.0 / (float(sig) ** 2)))
+    out = np.zeros((F, n), dtype=np.float32)
+    _check(lib().ldpc_ref_awgn_llr(_ptr(cw), frame0, F, n, seed, float(sig),
+                                   float(llr_scale), _ptr(out)),
+           "ldpc_ref_awgn_llr")
+    return out
+
+
+def quantize_i8(llr: np.ndarray, scale: float = 4.0, clip: int = 63) -> np.ndarray:
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    out = np.zeros(llr.shape, dtype=np.int8)
+    _check(lib().ldpc_ref_quantize_i8(_ptr(llr), _ptr(out), llr.size,
+                                      float(scale), int(clip)),
+           "ldpc_ref_quantize_i8")
+    return out
+
+
+def unpack_hard(hard: np.ndarray, n: int) -> np.ndarray:
+    """[F][ceil(n/32)] LSB-first words -> u8[F][n] bits."""
+    hard = np.ascontiguousarray(hard, dtype=np.uint32)
+    by = hard.view(np.uint8).reshape(hard.shape[0], -1)
+    bits = np.unpackbits(by, axis=1, bitorder="little")
+    return bits[:, :n]
