@@ -1,0 +1,405 @@
+"""Throughput benchmark: layered min-sum decoding of the N=1944, Z=81, R=5/6
+Wi-Fi-6-shaped code on GB300.
+
+One step = decoding the whole workload once: three batches of 262,144
+frames at Eb/N0 = 3.5, 4.0 and 4.5 dB, int8 packed four frames per word,
+max 20 iterations with syndrome early stop.  Inputs are generated on the GPU
+(Philox info bits, direct encoder, AWGN, quantiser) before timing and stay
+resident in HBM (each batch's 510 MB of packed LLRs exceeds the 129 MB L2,
+so no flush is needed between steps).  The FP32 decoder is timed on the same
+frames and reported beside it.
+
+Prints one JSON line (rank 0).  With --impl reference it times the CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+EBN0 = (3.5, 4.0, 4.5)
+MAX_ITERS = 20
+WORKLOAD = ("wifi6-shaped N=1944 Z=81 R=5/6 (seeded 4x24 base matrix, seed 2), "
+            "3 x 262144 frames at Eb/N0 3.5/4.0/4.5 dB, max 20 iterations, early stop")
+METRIC = "info Gbit/s, plain layered min-sum decode"
+# Algorithmic operations per edge per iteration (per frame, or per packed
+# word of four frames): pass 1 = 9 (message rebuild 2, subtract, abs, min1,
+# max, min2, argmin, sign xor), pass 2 = 4 (select, sign, add, sign store),
+# syndrome = 2 (hard decision, xor); per row per iteration 4 (two scalings,
+# sign extraction, state store).
+OPS_PER_EDGE = 13 + 2
+OPS_PER_ROW = 4
+SMS = 152
+LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _profile_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (its hash is recorded beside the number)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    src = os.path.join(ROOT, "paper_2306_12063_gb300", "csrc", "ldpc_decode.cu")
+    try:
+        txt = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.e+]+)", txt)
+    if not m or not t or m.group(1) != digest:
+        return None
+    return float(t.group(1))
+
+
+def _alg_ops(code_e: int, code_m: int, iters_sum: int, words: bool) -> float:
+    ops = iters_sum * (OPS_PER_EDGE * code_e + OPS_PER_ROW * code_m)
+    return ops / 4.0 if words else float(ops)
+
+
+# --------------------------------------------------------------------------- oracle
+
+def run_oracle_sample(frames: int, ebn0: float, threads: int, dtype: str = "i8"):
+    """Oracle (as it stands) on `frames` frames of the 4.0 dB batch, decoded on
+    a thread pool in blocks of 10 frames per task (ctypes releases the GIL).
+    Returns (info bits decoded, seconds)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    shape = synth.wifi_n1944_r56()
+    rc = oracle.RefCode(shape.hbm, shape.z)
+    sigma = synth.ebn0_db_to_sigma(ebn0, rc.k / rc.n)
+    frame0 = EBN0.index(ebn0) * 262144
+    blocks = [(f, min(10, frames - f)) for f in range(0, frames, 10)]
+
+    def gen(b):
+        f, n = b
+        info = oracle.gen_info(1, frame0 + f, n, rc.k)
+        llr = oracle.awgn_llr(rc.encode(info), frame0 + f, 1, sigma)
+        return oracle.quantize_i8(llr) if dtype == "i8" else llr
+
+    with ThreadPoolExecutor(threads) as ex:
+        inputs = list(ex.map(gen, blocks))
+
+    def dec(x):
+        if dtype == "i8":
+            return rc.decode_layered_i8(x, MAX_ITERS, True, True, want_post=False)[1]
+        return rc.decode_layered_f32(x, MAX_ITERS, 0.75, True, True, want_post=False)[1]
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(dec, inputs))
+    dt = time.perf_counter() - t0
+    return frames * rc.k, dt
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    frames = args.ref_frames
+    for _ in range(args.warmup):
+        run_oracle_sample(min(frames, 200), 4.0, threads)
+    bits = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        b, s = run_oracle_sample(frames, 4.0, threads)
+        bits += b
+        secs += s
+    gbps = bits / secs / 1e9
+    sample = (f"{frames} frames of the 4.0 dB batch per step, int8, max 20 iterations, "
+              f"early stop, {threads} threads in blocks of 10 frames")
+    line = {"impl": "reference", "metric": METRIC, "value": gbps, "unit": "Gbit/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": gbps, "unit": "Gbit/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbps, "unit": "Gbit/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=262144, help="frames per Eb/N0 batch")
+    ap.add_argument("--ref-frames", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    ws, rank, local = _dist()
+    import torch
+    import paper_2306_12063_gb300 as ldpc
+    from paper_2306_12063_gb300 import _build
+    from paper_2306_12063_gb300.workload import make_batch
+
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+        dist.barrier()
+    ldpc.load()
+
+    shape = synth.wifi_n1944_r56()
+    code = ldpc.Code(shape.hbm, shape.z, device=f"cuda:{local}")
+    E = sum(int((shape.hbm[i] >= 0).sum()) for i in range(shape.mb)) * shape.z
+    F = args.frames
+    batches = []
+    for b, eb in enumerate(EBN0):
+        frame0 = (rank * len(EBN0) + b) * F
+        bt = make_batch(code, F, frame0, eb, keep_cw=False)
+        if args.no_fp32:
+            bt.llr = None
+        batches.append(bt)
+    torch.cuda.synchronize()
+    dev = torch.device("cuda", local)
+    outs = [(torch.empty((F, code.nwords), dtype=torch.int32, device=dev),
+             torch.empty((F,), dtype=torch.int32, device=dev), None) for _ in EBN0]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def step(dtype, events=None):
+        for i, bt in enumerate(batches):
+            if events is not None:
+                events[i][0].record(stream)
+            if dtype == ldpc.I8X4:
+                code.decode(bt.q, frames=F, dtype=ldpc.I8X4, max_iters=MAX_ITERS,
+                            early_stop=True, out=outs[i])
+            else:
+                code.decode(bt.llr, dtype=ldpc.F32, max_iters=MAX_ITERS, early_stop=True,
+                            out=outs[i])
+            if events is not None:
+                events[i][1].record(stream)
+
+    def timed(dtype, steps):
+        for _ in range(args.warmup):
+            step(dtype)
+        barrier()
+        ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in EBN0]
+              for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            t0.record(stream)
+            for s in range(steps):
+                step(dtype, ev[s])
+            t1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        total_ms = t0.elapsed_time(t1)
+        kern_ms = [e[0].elapsed_time(e[1]) for st in ev for e in st]
+        if pg is not None:
+            tt = torch.tensor([total_ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        iters_sum = sum(int(o[1].sum().item()) for o in outs)
+        return total_ms, kern_ms, iters_sum, clk.summary()
+
+    res = {}
+    i8_ms, i8_kern, i8_iters, i8_clk = timed(ldpc.I8X4, args.steps)
+    bits_per_step = len(EBN0) * F * code.k * ws
+    value = bits_per_step * args.steps / (i8_ms * 1e-3) / 1e9
+
+    # FER / iteration statistics of the last decode (not timed)
+    fer = {}
+    for i, (eb, bt) in enumerate(zip(EBN0, batches)):
+        st = code.frame_stats(bt.info, outs[i][0], outs[i][1], MAX_ITERS).cpu().numpy()
+        fer[str(eb)] = {"fer": float(st[1]) / F, "ber": float(st[0]) / (F * code.k),
+                        "undetected_frames": int(st[2]), "mean_iters": float(st[3]) / F}
+
+    clk = i8_clk or {}
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak_tops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12
+    launch_s = (sum(i8_kern) / len(i8_kern)) * 1e-3
+    ops_per_launch = _alg_ops(E, code.m, i8_iters, True) / len(EBN0)
+    ach_tops = ops_per_launch / launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": ach_tops, "peak": peak_tops, "unit": "Tops/s",
+                "frac": ach_tops / peak_tops,
+                "traffic": _profile_traffic("ldpc_decode_i8_wifi1944"),
+                "kernel": "decode_kernel<true> (int8x4)",
+                "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz "
+                              "(median SM clock sampled during the timed region)",
+                "hbm_gbs": (len(EBN0) * ((F + 3) // 4) * code.n * 4 +
+                            len(EBN0) * F * (code.nwords * 4 + 4)) / len(EBN0)
+                           / launch_s / 1e9,
+                "hbm_frac_of_measured": None}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        roofline["hbm_frac_of_measured"] = roofline["hbm_gbs"] / float(peaks["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
+
+    if not args.no_fp32:
+        f_steps = max(1, args.steps // 2)
+        f_ms, f_kern, f_iters, f_clk = timed(ldpc.F32, f_steps)
+        f_launch = (sum(f_kern) / len(f_kern)) * 1e-3
+        f_ops = _alg_ops(E, code.m, f_iters, False) / len(EBN0)
+        f_mhz = (f_clk or {}).get("sm_mhz") or mhz
+        f_peak = SMS * LANES_PER_SM * f_mhz * 1e6 / 1e12
+        res["fp32"] = {"value": bits_per_step * f_steps / (f_ms * 1e-3) / 1e9,
+                       "unit": "Gbit/s", "steps": f_steps, "ms_per_step": f_ms / f_steps,
+                       "roofline": {"bound": "alu", "achieved": f_ops / f_launch / 1e12,
+                                    "peak": f_peak, "unit": "Tops/s",
+                                    "frac": f_ops / f_launch / 1e12 / f_peak,
+                                    "traffic": _profile_traffic("ldpc_decode_f32_wifi1944")},
+                       "mean_iters": f_iters / (len(EBN0) * F)}
+
+    e2e = None
+    if not args.no_e2e:
+        host_q = [bt.q.cpu().pin_memory() for bt in batches]
+        h_hard = [torch.empty((F, code.nwords), dtype=torch.int32).pin_memory() for _ in EBN0]
+        h_iters = [torch.empty((F,), dtype=torch.int32).pin_memory() for _ in EBN0]
+        chunk = 32768
+        wsb = torch.empty(code.host_workspace_bytes(ldpc.I8X4, chunk), dtype=torch.uint8,
+                          device=dev)
+
+        def e2e_step():
+            for i in range(len(EBN0)):
+                code.decode_host(host_q[i], F, ldpc.I8X4, h_hard[i], h_iters[i], wsb, chunk,
+                                 max_iters=MAX_ITERS, early_stop=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        e_steps = max(1, args.steps // 2)
+        a.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = a.elapsed_time(b_)
+        if pg is not None:
+            tt = torch.tensor([e_ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": bits_per_step * e_steps / (e_ms * 1e-3) / 1e9, "unit": "Gbit/s",
+               "h2d_bytes_per_step": sum(int(h.numel()) * 4 for h in host_q),
+               "d2h_bytes_per_step": sum(int(h.numel()) * 4 for h in h_hard) +
+               sum(int(h.numel()) * 4 for h in h_iters),
+               "steps": e_steps, "chunk_frames": chunk,
+               "api": "ldpc_decode_host (pinned host buffers, copies inside the timed region)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        bits, secs = run_oracle_sample(args.ref_frames, 4.0, threads)
+        cpu = {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": threads,
+               "kind": "oracle",
+               "sample": f"{args.ref_frames} frames of the 4.0 dB batch, int8, max 20 "
+                         f"iterations, early stop, {threads} threads, blocks of 10 frames"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": i8_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": len(EBN0) * F,
+                           "decoder": "int8 packed 4 frames/word, normalisation (3m)>>2",
+                           "parallelism": f"frames sharded over {ws} GPU(s), no collective",
+                           "l2": "inputs larger than L2 (510 MB of packed LLRs per batch)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": len(EBN0) * args.steps, "clocks": i8_clk,
+                "mean_iters": i8_iters / (len(EBN0) * F), "fer": fer}
+        line.update(res)
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * libldpc -- layered single-scan min-sum decoding and direct encoding of
+ * QC-LDPC codes shaped like the IEEE 802.11 (Wi-Fi 6) and IEEE 802.16
+ * (WiMAX) codes, on NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow Palenik & Szitkey, "High Throughput Open-Source
+ * Implementation of Wi-Fi 6 and WiMAX LDPC Encoder and Decoder"
+ * (arXiv 2306.12063), cited below by section and equation.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers, h_* are host pointers.
+ *    The caller owns every buffer; the library owns only the code handle and
+ *    the small device tables inside it.
+ *  - Work is enqueued on the given stream and returns before it runs.
+ *    Argument errors are detected on the host and returned at once; nothing
+ *    is enqueued then.  No call aborts, exits or traps.
+ *  - A status other than LDPC_OK leaves a message for ldpc_last_error() on
+ *    the calling thread.
+ *  - Circulant convention: base-matrix entry s >= 0 at block (i, j) places
+ *    the one of check row i*Z + r at variable j*Z + (r + s) mod Z.
+ *  - Bits are one per byte (0/1) unless stated; packed hard decisions use
+ *    bit (n % 32) of 32-bit word n / 32, ceil(N / 32) words per frame.
+ *  - Hard decision, eq. (21): bit = 0 if the posterior is > 0, else 1.
+ */
+#ifndef LDPC_H
+#define LDPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The CUDA runtime's stream handle type (declared here so that this header
+ * needs no CUDA include).  NULL is the legacy default stream. */
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+    LDPC_OK = 0,
+    LDPC_ERR_INVALID_ARG = 1,    /* a pointer, size or flag is out of range */
+    LDPC_ERR_BAD_STRUCTURE = 2,  /* base matrix lacks the eq. (3)-(7) shape */
+    LDPC_ERR_NOMEM = 3,          /* a host or device allocation failed */
+    LDPC_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    LDPC_ERR_TIMEOUT = 5,        /* a bounded wait ran out */
+    LDPC_ERR_UNSUPPORTED = 6     /* valid input outside what the kernels handle */
+} ldpc_status;
+
+typedef enum {
+    LDPC_F32 = 0,   /* channel LLRs float[F][N]; posteriors float[F][N] */
+    LDPC_I8X4 = 1   /* channel LLRs int8 packed four frames per 32-bit word,
+                       uint32[ceil(F/4)][N], byte b of word (g, n) = frame
+                       4g + b; posteriors int8[F][N] */
+} ldpc_dtype;
+
+typedef struct ldpc_code ldpc_code;   /* opaque; created and freed here */
+
+/* Selects the GPU that later calls (and code handles created afterwards)
+ * use.  Call it once per host thread before the first ldpc_code_create when
+ * the process uses a GPU other than 0. */
+ldpc_status ldpc_set_device(int device);
+
+/* Builds a code from its base (model) matrix H_bm (Section 1, eq. 2):
+ * hbm is a host array, row-major mb x nb int16, entries -1 (zero block) or a
+ * cyclic shift in [0, z).  The array is copied.
+ * Requires 3 <= mb < nb <= 32, 1 <= z <= 384 and the parity structure the
+ * direct encoder needs (eq. 3-7): column Kb = nb - mb (h_b) has equal
+ * non-negative entries in rows 0 and mb-1 and exactly one more non-negative
+ * entry, at a row y in 1..mb-2; columns Kb+1+t, t = 0..mb-2 (H_b2') hold 0
+ * at rows t and t+1 and -1 elsewhere.  Otherwise LDPC_ERR_BAD_STRUCTURE.
+ * On success *out receives a handle bound to the current device; it holds a
+ * few kilobytes of device memory for the per-layer edge table. */
+ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z,
+                             ldpc_code **out);
+
+/* Frees the handle (no-op on NULL).  Pending work that uses it must have
+ * finished. */
+void ldpc_code_destroy(ldpc_code *code);
+
+/* N = nb z, K = (nb - mb) z, M = mb z, z, and the largest check-row degree
+ * max g(m) (Section 1).  Any output pointer may be NULL. */
+ldpc_status ldpc_code_info(const ldpc_code *code, int *n, int *k, int *m,
+                           int *z, int *max_row_deg);
+
+/* Synthetic info bits: bit k of frame f = frame0 + i is bit (k % 32) of
+ * word (k / 32) % 4 of Philox4x32-10 (Salmon et al., SC'11) at counter
+ * {k / 128, f mod 2^32, f / 2^32, 0} under key {seed mod 2^32,
+ * (seed / 2^32) ^ 0x494E464F}.  d_info: uint8[frames][k]. */
+ldpc_status ldpc_gen_info(uint64_t seed, int64_t frame0, int64_t frames, int k,
+                          uint8_t *d_info, cudaStream_t stream);
+
+/* Direct encoder of Section 2, eq. (8)-(15): d_info uint8[frames][K] (0/1)
+ * -> d_code uint8[frames][N] = [info | v_0 | v_1 | ... | v_{Mb-1}] with
+ * S_i = sum_j P_{H(i,j)} u_j (eq. 15), v_0 = P^{-1}_{H(y,Kb)} sum_i S_i
+ * (eq. 12), v_1 = P_{H(0,Kb)} v_0 + S_0 (eq. 13) and
+ * v_{i+1} = v_i + P_{H(i,Kb)} v_0 + S_i (eq. 14), all over GF(2). */
+ldpc_status ldpc_encode(const ldpc_code *code, const uint8_t *d_info,
+                        uint8_t *d_code, int64_t frames, cudaStream_t stream);
+
+/* BPSK over AWGN and the channel LLR, eq. (16)-(17): for frame
+ * f = frame0 + i and position n, g is Gaussian number n % 4 of the
+ * Box-Muller pair-of-pairs drawn from Philox4x32-10 at counter
+ * {n / 4, f mod 2^32, f / 2^32, 0} under key {seed mod 2^32,
+ * (seed / 2^32) ^ 0x4E4F4953}; y = (1 - 2 c) + sigma g and
+ * llr = y * llr_scale (llr_scale = 2 / sigma^2 for eq. 17).  The logarithm,
+ * sine and cosine are evaluated with fixed series in correctly rounded
+ * float arithmetic, so the output does not depend on the math library.
+ * d_code uint8[frames][n] -> d_llr float[frames][n]. */
+ldpc_status ldpc_awgn_llr(const uint8_t *d_code, int64_t frame0, int64_t frames,
+                          int n, uint64_t seed, float sigma, float llr_scale,
+                          float *d_llr, cudaStream_t stream);
+
+/* Fixed-point channel input (Section 5, narrowed to 8 bits):
+ * q = rint(clamp(scale * llr, -clip, clip)) with round-half-to-even, packed
+ * four frames per word: d_llr float[frames][n] -> d_q uint32[ceil(frames/4)][n],
+ * byte b of word (g, n) = frame 4g + b.  Bytes of frames >= frames (the pad
+ * of the last group) are set to +clip.  0 <= clip <= 127. */
+ldpc_status ldpc_quantize_pack_i8(const float *d_llr, uint32_t *d_q,
+                                  int64_t frames, int n, float scale, int clip,
+                                  cudaStream_t stream);
+
+typedef struct {
+    int max_iters;   /* 1..1000 full iterations */
+    float alpha;     /* message scale when normalise = 1 (FP32 path) */
+    int normalise;   /* 0: plain min-sum, eq. (23); 1: scaled messages.
+                        LDPC_I8X4 scales by (3 |m|) >> 2 and requires
+                        alpha == 0.75 */
+    int early_stop;  /* 1: stop a frame after the first full iteration whose
+                        hard decisions satisfy H x^T = 0 (Section 4, step 4) */
+} ldpc_decode_params;
+
+/* Layered single-scan min-sum decoding (Section 4, eq. 20, 22, 23): for
+ * every iteration, block rows (layers) 0..Mb-1 in order; within a layer each
+ * check row m computes Z_mn = Z_n - L_mn for its variables, the new
+ * messages L_mn = s * min_{n' != n} |Z_mn'| * prod_{n' != n} sgn Z_mn' (s =
+ * alpha or 1), and writes Z_n = Z_mn + L_mn.  Only the compressed messages
+ * (two magnitudes, the argmin and the sign bits per row) are kept.
+ *   d_llr   LDPC_F32: float[frames][N];  LDPC_I8X4: uint32[ceil(frames/4)][N]
+ *           (as written by ldpc_quantize_pack_i8; int8 values must lie in
+ *           [-127, 127]).  16-byte alignment enables the bulk-copy path.
+ *   d_hard  uint32[frames][ceil(N/32)] hard decisions of eq. (21).
+ *   d_iters int32[frames]: the iteration at which the syndrome became zero,
+ *           or max_iters.
+ *   d_post  NULL, or posteriors Z_n: float[frames][N] / int8[frames][N].
+ * A frame that stops early has its outputs written at that iteration and
+ * never changed afterwards.  LDPC_I8X4 saturates every Z_mn and Z_n to
+ * [-127, 127].  Rows of degree above 27 are LDPC_ERR_UNSUPPORTED. */
+ldpc_status ldpc_decode_layered_minsum(const ldpc_code *code, ldpc_dtype dtype,
+                                       const void *d_llr, int64_t frames,
+                                       const ldpc_decode_params *params,
+                                       uint32_t *d_hard, int32_t *d_iters,
+                                       void *d_post, cudaStream_t stream);
+
+/* Error counts of decoded frames against the sent info bits (the
+ * evaluation of Section 6.1).  d_counters int64[4 + max_iters + 1] is
+ * overwritten with: [0] info-bit errors, [1] frame errors (any info bit
+ * wrong), [2] undetected frame errors (hard decisions satisfy every check
+ * but the info bits are wrong), [3] sum of d_iters, [4 + t] number of frames
+ * with d_iters == t. */
+ldpc_status ldpc_frame_stats(const ldpc_code *code, const uint8_t *d_info,
+                             const uint32_t *d_hard, const int32_t *d_iters,
+                             int64_t frames, int max_iters, int64_t *d_counters,
+                             cudaStream_t stream);
+
+/* Device bytes that ldpc_decode_host needs as workspace for a given chunk
+ * of frames (a multiple of 4). */
+size_t ldpc_decode_host_workspace_bytes(const ldpc_code *code, ldpc_dtype dtype,
+                                        int64_t chunk_frames);
+
+/* End-to-end decode of host-resident data: copies h_llr to the device in
+ * chunks of chunk_frames frames, decodes each chunk, and copies hard
+ * decisions and iteration counts back, overlapping the copies of one chunk
+ * with the decoding of the next on two internal streams ordered after and
+ * before `stream`.  Host buffers should be page-locked for the copies to run
+ * asynchronously.  d_workspace must hold ldpc_decode_host_workspace_bytes.
+ * Layouts as in ldpc_decode_layered_minsum (no posteriors). */
+ldpc_status ldpc_decode_host(const ldpc_code *code, ldpc_dtype dtype,
+                             const void *h_llr, int64_t frames,
+                             const ldpc_decode_params *params,
+                             uint32_t *h_hard, int32_t *h_iters,
+                             void *d_workspace, size_t workspace_bytes,
+                             int64_t chunk_frames, cudaStream_t stream);
+
+/* Waits for `stream` to drain, polling for at most timeout_s seconds
+ * (LDPC_ERR_TIMEOUT if it has not), then reads the handle's device status
+ * word: a kernel whose bounded wait on a bulk copy ran out reports it there
+ * and the call returns LDPC_ERR_TIMEOUT.  The status word is cleared. */
+ldpc_status ldpc_sync(const ldpc_code *code, cudaStream_t stream,
+                      double timeout_s);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *ldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_H */

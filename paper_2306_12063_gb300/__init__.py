@@ -1,0 +1,245 @@
+"""Python binding of libldpc (include/ldpc.h): layered min-sum decoding and
+direct encoding of QC-LDPC codes on GB300.
+
+This layer only marshals arguments: torch supplies device memory and the
+current CUDA stream, every step of the work runs in the library's kernels.
+Importing works without a GPU; any call that would launch work raises if the
+compiled library is missing (run ``_build.build()``), never falls back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["LdpcError", "Code", "load", "gen_info", "awgn_llr", "quantize_pack_i8",
+           "F32", "I8X4", "symbols"]
+
+F32 = 0
+I8X4 = 1
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_STRUCTURE", 3: "NOMEM", 4: "CUDA",
+           5: "TIMEOUT", 6: "UNSUPPORTED"}
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libldpc {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("alpha", ctypes.c_float),
+                ("normalise", ctypes.c_int), ("early_stop", ctypes.c_int)]
+
+
+_lib = None
+
+
+def symbols():
+    """Function names declared in include/ldpc.h."""
+    import re
+    hdr = os.path.join(_build.ROOT, "include", "ldpc.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(ldpc_\w+)\s*\(", txt, re.M)))
+
+
+def load(build_if_missing: bool = False):
+    """The loaded library (ctypes).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libldpc is not built ({_build.LIB} missing); "
+                               "run paper_2306_12063_gb300._build.build()")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, u64, f32, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                  ctypes.c_uint64, ctypes.c_float, ctypes.c_size_t)
+    P = ctypes.POINTER
+    sig = {
+        "ldpc_set_device": ([i32], i32),
+        "ldpc_code_create": ([vp, i32, i32, i32, P(vp)], i32),
+        "ldpc_code_destroy": ([vp], None),
+        "ldpc_code_info": ([vp, P(i32), P(i32), P(i32), P(i32), P(i32)], i32),
+        "ldpc_gen_info": ([u64, i64, i64, i32, vp, vp], i32),
+        "ldpc_encode": ([vp, vp, vp, i64, vp], i32),
+        "ldpc_awgn_llr": ([vp, i64, i64, i32, u64, f32, f32, vp, vp], i32),
+        "ldpc_quantize_pack_i8": ([vp, vp, i64, i32, f32, i32, vp], i32),
+        "ldpc_decode_layered_minsum": ([vp, i32, vp, i64, P(_Params), vp, vp, vp, vp], i32),
+        "ldpc_frame_stats": ([vp, vp, vp, vp, i64, i32, vp, vp], i32),
+        "ldpc_decode_host_workspace_bytes": ([vp, i32, i64], sz),
+        "ldpc_decode_host": ([vp, i32, vp, i64, P(_Params), vp, vp, vp, sz, i64, vp], i32),
+        "ldpc_sync": ([vp, vp, ctypes.c_double], i32),
+        "ldpc_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        msg = load().ldpc_last_error().decode(errors="replace")
+        raise LdpcError(status, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def _bind_device(dev):
+    torch = _torch()
+    idx = torch.device(dev).index
+    if idx is None:
+        idx = torch.cuda.current_device()
+    _check(load().ldpc_set_device(idx))
+    return idx
+
+
+class Code:
+    """A QC-LDPC code from its base matrix (Section 1, eq. 2) on one GPU."""
+
+    def __init__(self, hbm, z: int, device="cuda"):
+        hbm = np.ascontiguousarray(hbm, dtype=np.int16)
+        self.device_index = _bind_device(device)
+        self.hbm = hbm
+        self._h = ctypes.c_void_p()
+        _check(load().ldpc_code_create(hbm.ctypes.data_as(ctypes.c_void_p), hbm.shape[0],
+                                       hbm.shape[1], int(z), ctypes.byref(self._h)))
+        vals = [ctypes.c_int() for _ in range(5)]
+        _check(load().ldpc_code_info(self._h, *[ctypes.byref(v) for v in vals]))
+        self.n, self.k, self.m, self.z, self.max_row_deg = [v.value for v in vals]
+        self.nwords = (self.n + 31) // 32
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.ldpc_code_destroy(h)
+            self._h = None
+
+    @property
+    def device(self):
+        return _torch().device("cuda", self.device_index)
+
+    def encode(self, info, out=None, stream=None):
+        """eq. (8)-(15): uint8[F][K] -> uint8[F][N] on the GPU."""
+        torch = _torch()
+        F = info.shape[0]
+        if out is None:
+            out = torch.empty((F, self.n), dtype=torch.uint8, device=info.device)
+        _check(load().ldpc_encode(self._h, _ptr(info), _ptr(out), F, _stream(stream)))
+        return out
+
+    def decode(self, llr, frames: Optional[int] = None, dtype: int = F32, max_iters: int = 10,
+               alpha: float = 0.75, normalise: bool = True, early_stop: bool = False,
+               want_post: bool = False, out=None, stream=None):
+        """Layered min-sum (Section 4).  llr: float32[F][N] (F32) or the packed
+        int32/uint32 [ceil(F/4)][N] words of quantize_pack_i8 (I8X4).
+        Returns (hard int32[F][ceil(N/32)], iters int32[F], post or None)."""
+        torch = _torch()
+        if frames is None:
+            frames = llr.shape[0] if dtype == F32 else 4 * llr.shape[0]
+        dev = llr.device
+        if out is None:
+            hard = torch.empty((frames, self.nwords), dtype=torch.int32, device=dev)
+            iters = torch.empty((frames,), dtype=torch.int32, device=dev)
+            post = None
+            if want_post:
+                post = torch.empty((frames, self.n),
+                                   dtype=torch.float32 if dtype == F32 else torch.int8,
+                                   device=dev)
+        else:
+            hard, iters, post = out
+        p = _Params(int(max_iters), float(alpha), int(bool(normalise)), int(bool(early_stop)))
+        _check(load().ldpc_decode_layered_minsum(self._h, int(dtype), _ptr(llr), int(frames),
+                                                 ctypes.byref(p), _ptr(hard), _ptr(iters),
+                                                 _ptr(post), _stream(stream)))
+        return hard, iters, post
+
+    def frame_stats(self, info, hard, iters, max_iters: int, out=None, stream=None):
+        """int64[4 + max_iters + 1]: bit errors, frame errors, undetected
+        errors, iteration sum, iteration histogram."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((5 + max_iters,), dtype=torch.int64, device=hard.device)
+        _check(load().ldpc_frame_stats(self._h, _ptr(info), _ptr(hard), _ptr(iters),
+                                       int(hard.shape[0]), int(max_iters), _ptr(out),
+                                       _stream(stream)))
+        return out
+
+    def host_workspace_bytes(self, dtype: int, chunk_frames: int) -> int:
+        return int(load().ldpc_decode_host_workspace_bytes(self._h, int(dtype),
+                                                           int(chunk_frames)))
+
+    def decode_host(self, h_llr, frames: int, dtype: int, h_hard, h_iters, workspace,
+                    chunk_frames: int, max_iters: int = 20, alpha: float = 0.75,
+                    normalise: bool = True, early_stop: bool = True, stream=None):
+        """End-to-end decode of host (pinned) buffers through the library's
+        copy/decode pipeline; outputs land in h_hard / h_iters."""
+        p = _Params(int(max_iters), float(alpha), int(bool(normalise)), int(bool(early_stop)))
+        _check(load().ldpc_decode_host(self._h, int(dtype), _ptr(h_llr), int(frames),
+                                       ctypes.byref(p), _ptr(h_hard), _ptr(h_iters),
+                                       _ptr(workspace), int(workspace.numel()),
+                                       int(chunk_frames), _stream(stream)))
+
+    def sync(self, timeout_s: float = 60.0, stream=None):
+        _check(load().ldpc_sync(self._h, _stream(stream), float(timeout_s)))
+
+
+def gen_info(seed: int, frame0: int, frames: int, k: int, device="cuda", out=None,
+             stream=None):
+    """Philox info bits uint8[frames][k] on the GPU."""
+    torch = _torch()
+    _bind_device(device)
+    if out is None:
+        out = torch.empty((frames, k), dtype=torch.uint8, device=device)
+    _check(load().ldpc_gen_info(int(seed), int(frame0), int(frames), int(k), _ptr(out),
+                                _stream(stream)))
+    return out
+
+
+def awgn_llr(cw, frame0: int, seed: int, sigma: float, llr_scale: Optional[float] = None,
+             out=None, stream=None):
+    """eq. (16)-(17) channel on the GPU; llr_scale defaults to the float32 value
+    of 2 / sigma^2."""
+    torch = _torch()
+    F, n = cw.shape
+    sig = np.float32(sigma)
+    if llr_scale is None:
+        llr_scale = float(np.float32(2.0 / (float(sig) ** 2)))
+    if out is None:
+        out = torch.empty((F, n), dtype=torch.float32, device=cw.device)
+    _check(load().ldpc_awgn_llr(_ptr(cw), int(frame0), int(F), int(n), int(seed), float(sig),
+                                float(llr_scale), _ptr(out), _stream(stream)))
+    return out
+
+
+def quantize_pack_i8(llr, scale: float = 4.0, clip: int = 63, out=None, stream=None):
+    """float32[F][N] -> int32[ceil(F/4)][N] words of four int8 frames."""
+    torch = _torch()
+    F, n = llr.shape
+    if out is None:
+        out = torch.empty(((F + 3) // 4, n), dtype=torch.int32, device=llr.device)
+    _check(load().ldpc_quantize_pack_i8(_ptr(llr), _ptr(out), int(F), int(n), float(scale),
+                                        int(clip), _stream(stream)))
+    return out

@@ -1,0 +1,171 @@
+// Internal definitions shared by the libldpc translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ldpc.h"
+
+namespace ldpc {
+
+constexpr int kMaxNb = 32;          // block columns (row degree <= nb)
+constexpr int kMaxRowDeg = 27;      // sign bits + 5-bit argmin share one word
+constexpr int kMaxZ = 384;        // 4 N < 65536: byte offsets fit uint16
+constexpr int kMaxIters = 1000;
+
+// Device status word bits (set by kernels, read and cleared by ldpc_sync).
+constexpr int kStatusCopyTimeout = 1;
+
+// Host-side record of a code; the device tables are built once at creation.
+struct Code {
+    int device = 0;
+    int mb = 0, nb = 0, kb = 0, z = 0, n = 0, k = 0, m = 0, y = 0;
+    int max_deg = 0, min_deg = 0, n_edges = 0;
+    int rpl = 0;                     // row slots per lane: ceil(z / 32)
+    std::vector<int16_t> hbm;        // [mb][nb]
+    std::vector<int> layer_off;      // [mb + 1] into the edge list
+    std::vector<int> edge_col;       // block column j of each edge (sorted per layer)
+    std::vector<int> edge_shift;     // its cyclic shift s
+    // device copies
+    int16_t *d_hbm = nullptr;        // [mb][nb] (encoder)
+    uint16_t *d_voff = nullptr;      // per-lane variable offsets, see make_voff
+    uint32_t *d_rowinfo = nullptr;   // [mb] layer degree and first edge
+    int *d_status = nullptr;         // device status word
+    cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    size_t voff_words = 0;           // uint16 entries in d_voff
+};
+
+// Kernel-side view of a code, passed by value.
+struct DevCode {
+    int n, k, m, z, mb, nb, kb, y;
+    int nwords;        // ceil(n / 32)
+    int rpl;           // row slots per lane
+    int n_edges;       // block edges (nonzeros of H_bm)
+    const int16_t *hbm;
+    const uint16_t *voff;     // [n_edges][rpl][32] variable index of each lane/slot/edge
+    const uint32_t *rowinfo;  // [mb] (first_edge << 8) | degree
+    int *status;
+};
+
+inline DevCode dev_view(const Code &c) {
+    DevCode d;
+    d.n = c.n; d.k = c.k; d.m = c.m; d.z = c.z; d.mb = c.mb; d.nb = c.nb;
+    d.kb = c.kb; d.y = c.y; d.nwords = (c.n + 31) / 32; d.rpl = c.rpl;
+    d.n_edges = c.n_edges; d.hbm = c.d_hbm; d.voff = c.d_voff;
+    d.rowinfo = c.d_rowinfo; d.status = c.d_status;
+    return d;
+}
+
+// Thread-local last-error message, set by fail().
+void set_error(const std::string &msg);
+ldpc_status fail(ldpc_status st, const std::string &msg);
+ldpc_status cuda_fail(cudaError_t e, const char *what);
+
+struct DecodeParams {
+    int max_iters;
+    float alpha;
+    int normalise;
+    int early_stop;
+};
+
+// Launchers (defined in the .cu files).
+ldpc_status launch_gen_info(uint64_t seed, int64_t frame0, int64_t frames, int k,
+                            uint8_t *d_info, cudaStream_t s);
+ldpc_status launch_encode(const Code &c, const uint8_t *d_info, uint8_t *d_code,
+                          int64_t frames, cudaStream_t s);
+ldpc_status launch_awgn(const uint8_t *d_code, int64_t frame0, int64_t frames, int n,
+                        uint64_t seed, float sigma, float scale, float *d_llr,
+                        cudaStream_t s);
+ldpc_status launch_quantize(const float *d_llr, uint32_t *d_q, int64_t frames, int n,
+                            float scale, int clip, cudaStream_t s);
+ldpc_status launch_stats(const Code &c, const uint8_t *d_info, const uint32_t *d_hard,
+                         const int32_t *d_iters, int64_t frames, int max_iters,
+                         int64_t *d_counters, cudaStream_t s);
+ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr,
+                          int64_t frames, const DecodeParams &p, uint32_t *d_hard,
+                          int32_t *d_iters, void *d_post, cudaStream_t s);
+
+}  // namespace ldpc
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace ldpc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make the barrier initialisation visible to the asynchronous (bulk copy) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) writes to the same addresses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+            smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, "
+        "0, p; }"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Byte-wise mask from the top bit of each byte: 0xFF where bit 7 is set.
+__device__ __forceinline__ uint32_t msb_bytes_to_mask(uint32_t x) {
+    uint32_t r;   // prmt selector nibble with bit 3 set replicates the byte's sign
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(x));
+    return r;
+}
+
+// Bitwise select: bits of b where m is 1, bits of a where m is 0.
+__device__ __forceinline__ uint32_t bsel(uint32_t a, uint32_t b, uint32_t m) {
+    return (a & ~m) | (b & m);
+}
+
+}  // namespace ldpc
+#endif
