@@ -70,21 +70,31 @@ static bool encodable_structure(const int16_t *h, int mb, int nb, int *y_out,
     return true;
 }
 
-static void destroy_code(Code *c) {
-    if (!c) return;
+static void release(Code &c) {
     int prev = 0;
     cudaGetDevice(&prev);
-    cudaSetDevice(c->device);
-    cudaFree(c->d_hbm);
-    cudaFree(c->d_voff);
-    cudaFree(c->d_rowinfo);
-    cudaFree(c->d_status);
-    for (auto &s : c->aux)
+    cudaSetDevice(c.device);
+    cudaFree(c.d_hbm);
+    cudaFree(c.d_voff);
+    cudaFree(c.d_rowinfo);
+    cudaFree(c.d_status);
+    cudaFree(c.d_work);
+    for (auto &s : c.aux)
         if (s) cudaStreamDestroy(s);
-    for (auto &e : c->ev)
+    for (auto &e : c.ev)
         if (e) cudaEventDestroy(e);
     cudaSetDevice(prev);
-    delete c;
+}
+
+unsigned long long *work_slot(const Code &c, cudaStream_t s) {
+    const unsigned k = c.work_seq.fetch_add(1u) % kWorkSlots;
+    unsigned long long *p = c.d_work + k;
+    cudaError_t e = cudaMemsetAsync(p, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "cudaMemsetAsync work counter");
+        return nullptr;
+    }
+    return p;
 }
 
 static ldpc_status bind(const Code *c) {
@@ -185,6 +195,7 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     if (e == cudaSuccess) e = cudaMalloc(&c.d_voff, sizeof(uint16_t) * voff.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_rowinfo, sizeof(uint32_t) * mb);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_work, sizeof(unsigned long long) * kWorkSlots);
     if (e == cudaSuccess)
         e = cudaMemcpy(c.d_hbm, hbm, sizeof(int16_t) * mb * nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -198,8 +209,7 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
         ldpc_status st = (e == cudaErrorMemoryAllocation)
                              ? fail(LDPC_ERR_NOMEM, "ldpc_code_create: device allocation")
                              : cuda_fail(e, "ldpc_code_create");
-        Code *tmp = new Code(c);
-        destroy_code(tmp);
+        release(c);
         delete h;
         return st;
     }
@@ -209,8 +219,7 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
 
 void ldpc_code_destroy(ldpc_code *code) {
     if (!code) return;
-    Code *tmp = new Code(code->c);
-    destroy_code(tmp);
+    release(code->c);
     delete code;
 }
 

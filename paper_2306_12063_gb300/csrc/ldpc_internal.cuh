@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -37,7 +38,13 @@ struct Code {
     cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     size_t voff_words = 0;           // uint16 entries in d_voff
+    // Work counters of the decode kernels' dynamic frame scheduling: one
+    // 64-bit slot per launch, taken round-robin and zeroed on the launch's
+    // stream, so up to kWorkSlots launches may be in flight at once.
+    unsigned long long *d_work = nullptr;
+    mutable std::atomic<unsigned> work_seq{0};
 };
+constexpr int kWorkSlots = 64;
 
 // Kernel-side view of a code, passed by value.
 struct DevCode {
@@ -85,6 +92,9 @@ ldpc_status launch_quantize(const float *d_llr, uint32_t *d_q, int64_t frames, i
 ldpc_status launch_stats(const Code &c, const uint8_t *d_info, const uint32_t *d_hard,
                          const int32_t *d_iters, int64_t frames, int max_iters,
                          int64_t *d_counters, cudaStream_t s);
+// Zeroes the next work-counter slot on stream s and returns it (NULL and an
+// error message on failure).
+unsigned long long *work_slot(const Code &c, cudaStream_t s);
 ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr,
                           int64_t frames, const DecodeParams &p, uint32_t *d_hard,
                           int32_t *d_iters, void *d_post, cudaStream_t s);

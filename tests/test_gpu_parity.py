@@ -218,6 +218,20 @@ def test_i8_partial_groups(ldpc, frames):
     _assert_same(*_decode_both(ldpc, s, llr, "i8", 20, True))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("shape_name,frames", [("wifi648", 301), ("wifi1944", 150)])
+def test_dynamic_frame_handout(ldpc, monkeypatch, dtype, shape_name, frames):
+    """One resident block (four warps) decodes every frame: finished frames
+    are replaced through the work counter (per byte lane for int8), at low
+    Eb/N0 so iteration counts vary widely."""
+    monkeypatch.setenv("LDPC_DECODE_MAX_BLOCKS", "1")
+    s = SHAPES[shape_name]
+    _, _, _, llr, _ = oracle_inputs(s, frames, frame0=999, ebn0=1.0 if dtype == "f32" else 1.5)
+    want, got = _decode_both(ldpc, s, llr, dtype, 15, True)
+    _assert_same(want, got)
+    assert want[1].min() < 5 and want[1].max() == 15
+
+
 # ------------------------------------------------------- full-size sampled parity
 
 @pytest.mark.parametrize("dtype", ["i8", "f32"])
