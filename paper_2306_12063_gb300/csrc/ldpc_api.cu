@@ -170,20 +170,32 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     c.layer_off[mb] = static_cast<int>(c.edge_col.size());
     c.n_edges = c.layer_off[mb];
 
+    c.dslots = slot_class(c.max_deg);
+    const int D = c.dslots ? c.dslots : kMaxRowDeg;
     // Per-lane variable offsets: lane l of row slot t handles row r = l + 32 t
-    // of the layer; its variable on edge (j, s) is n = j Z + (r + s) mod Z.
-    // Stored as byte offsets into a float/uint32 posterior array (0 for the
-    // unused lanes r >= Z, which never touch memory).
-    std::vector<uint16_t> voff(static_cast<size_t>(c.n_edges) * c.rpl * 32, 0);
-    for (int q = 0; q < c.n_edges; ++q)
-        for (int t = 0; t < c.rpl; ++t)
-            for (int l = 0; l < 32; ++l) {
-                const int r = l + 32 * t;
-                if (r >= z) continue;
-                const int v = c.edge_col[q] * z + (r + c.edge_shift[q]) % z;
-                voff[(static_cast<size_t>(q) * c.rpl + t) * 32 + l] =
-                    static_cast<uint16_t>(4 * v);
-            }
+    // of a layer; its variable on edge (j, s) is n = j Z + (r + s) mod Z.
+    // Layout [layer][t][edge slot][lane] with D edge slots per row (the
+    // kernel's slot class); a layer of degree d fills slots D-d .. D-1 in edge
+    // order, so a slot sits at a fixed stride of 32 entries from the row's
+    // first one.  Entries are byte offsets into a 4-byte posterior array (0 for
+    // unused slots and for lanes r >= Z, which never read them).
+    std::vector<uint16_t> voff(static_cast<size_t>(mb) * c.rpl * D * 32, 0);
+    for (int i = 0; i < mb; ++i) {
+        const int d = c.layer_off[i + 1] - c.layer_off[i];
+        if (d > D) continue;   // rows above 27 edges are rejected by the decoders
+        for (int e = 0; e < d; ++e) {
+            const int q = c.layer_off[i] + e;
+            const int slot = D - d + e;
+            for (int t = 0; t < c.rpl; ++t)
+                for (int l = 0; l < 32; ++l) {
+                    const int r = l + 32 * t;
+                    if (r >= z) continue;
+                    const int v = c.edge_col[q] * z + (r + c.edge_shift[q]) % z;
+                    voff[((static_cast<size_t>(i) * c.rpl + t) * D + slot) * 32 + l] =
+                        static_cast<uint16_t>(4 * v);
+                }
+        }
+    }
     std::vector<uint32_t> rowinfo(mb);
     for (int i = 0; i < mb; ++i)
         rowinfo[i] = (static_cast<uint32_t>(c.layer_off[i]) << 8) |

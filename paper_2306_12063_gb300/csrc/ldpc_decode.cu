@@ -30,17 +30,16 @@ namespace ldpc {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kWaitLimit = 1u << 22;   // polls of a bulk-copy barrier
-constexpr int DMAX = kMaxRowDeg;
 
 // Row state words in shared memory (per check row):
-//   FP32: [m1, m2, meta, -]; m1, m2 scaled magnitudes; meta bits 0..26 hold
-//         the sign of L_mn for slot i at bit DMAX-1-i, bits 27..31 the argmin
-//         slot.
-//   int8: [M1, M2, IDX, SG0, SG1, SG2, SG3, -], one byte per frame: scaled
-//         magnitudes and argmin slot; SGk byte b bit u = sign of L_mn of frame
-//         b for slot 8k + u.
-constexpr int kRowWordsF32 = 4;
-constexpr int kRowWordsI8 = 8;
+//   FP32: [m1, m2, meta]; m1, m2 scaled magnitudes; meta bits 0..26 hold the
+//         sign of L_mn for slot i at bit DMAX-1-i, bits 27..31 the argmin slot.
+//   int8: [M1, M2, IDX, SG0 .. SG(k-1)] (padded to an even count), one byte
+//         per frame: scaled magnitudes and argmin slot; SGk byte b bit u =
+//         sign of L_mn of frame b for slot 8k + u.
+constexpr int kRowWordsF32 = 3;
+__host__ __device__ constexpr int sign_words(int dmax) { return (dmax + 7) / 8; }
+__host__ __device__ constexpr int row_words_i8(int dmax) { return (3 + sign_words(dmax) + 1) & ~1; }
 
 __device__ __forceinline__ uint32_t lds_u32(const uint32_t *base, uint32_t byte_off) {
     return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(base) + byte_off);
@@ -55,11 +54,14 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
     return r;
 }
-__device__ __forceinline__ uint32_t clamp_u16x2(uint32_t x, uint32_t lo, uint32_t hi) {
-    uint32_t r;
-    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(lo));
-    asm("min.u16x2 %0, %0, %1;" : "+r"(r) : "r"(hi));
-    return r;
+// min(max(a + b, lo), hi) on two 16-bit lanes holding non-negative values
+// (a + b < 65536 per lane); the add and the max issue as one instruction.
+__device__ __forceinline__ uint32_t add_clamp_u16x2(uint32_t a, uint32_t b, uint32_t lo,
+                                                    uint32_t hi) {
+    const uint32_t r = __viaddmax_u16x2(a, b, lo);
+    uint32_t o;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(hi));
+    return o;
 }
 // Bytes 0, 2 (resp. 1, 3) of x zero-extended into two 16-bit lanes.
 __device__ __forceinline__ uint32_t lanes_even(uint32_t x) { return prmt(x, 0u, 0x4240u); }
@@ -82,7 +84,7 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 #define LDPC_SLOTS(X)                                                                       \
     X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) \
     X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26)
-static_assert(DMAX == 27, "slot list must match kMaxRowDeg");
+static_assert(kMaxRowDeg == 27, "slot list must cover kMaxRowDeg slots");
 
 // ---------------------------------------------------------------------------
 // FP32 layer: eq. (22) Z_mn = Z_n - L_mn; eq. (23) new L_mn from the
@@ -90,39 +92,50 @@ static_assert(DMAX == 27, "slot list must match kMaxRowDeg");
 // single-scan form Z_n = Z_mn + L_mn.  Each float operation is an explicitly
 // rounded intrinsic, so no multiply-add is ever contracted.
 // ---------------------------------------------------------------------------
+template <int DMAX>
 __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t *Zs,
                                           uint32_t *rows, int lane, bool norm, float alpha) {
     const uint32_t ri = __ldg(c.rowinfo + layer);
-    const int d = ri & 255, e0 = static_cast<int>(ri >> 8);
+    const int d = ri & 255;
     const int start = DMAX - d;
-    const int stride = c.rpl * 32;
     for (int t = 0; t < c.rpl; ++t) {
         const int r = lane + 32 * t;
         if (r >= c.z) break;
-        uint4 *rs = reinterpret_cast<uint4 *>(rows + (layer * c.z + r) * kRowWordsF32);
-        const uint4 st = *rs;
-        const float m1 = __uint_as_float(st.x), m2 = __uint_as_float(st.y);
-        const uint32_t meta = st.z;
+        uint32_t *rs = rows + (layer * c.z + r) * kRowWordsF32;
+        const float m1 = __uint_as_float(rs[0]), m2 = __uint_as_float(rs[1]);
+        const uint32_t meta = rs[2];
         const int idx = static_cast<int>(meta >> 27);
-        const int vb = (e0 * c.rpl + t) * 32 + lane - start * stride;   // slot i: vb + i * stride
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
         uint32_t off[DMAX];
         float Q[DMAX];
+        // pass 1 in three computed-jump phases so that all loads of the row are
+        // in flight together: offsets, posteriors, then the arithmetic
+        switch (start) {
+#define A1(i) \
+    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
+            LDPC_SLOTS(A1)
+#undef A1
+            default: break;
+        }
+        switch (start) {
+#define B1(i) \
+    case i: if constexpr ((i) < DMAX) { Q[i] = __uint_as_float(lds_u32(Zs, off[i])); }
+            LDPC_SLOTS(B1)
+#undef B1
+            default: break;
+        }
         float mn1 = __int_as_float(0x7F800000), mn2 = mn1;
-        int id = 0;
         uint32_t sx = 0;
         switch (start) {
 #define P1(i)                                                                                \
-    case i: {                                                                                \
-        off[i] = __ldg(c.voff + vb + (i) * stride);                                                   \
-        const float zv = __uint_as_float(lds_u32(Zs, off[i]));                               \
+    case i: if constexpr ((i) < DMAX) {                                                                                \
         const float mag = (idx == (i)) ? m2 : m1;                                            \
         const float L = __uint_as_float(__float_as_uint(mag) |                               \
                                         ((meta << ((i) + 32 - DMAX)) & 0x80000000u));        \
-        const float q = __fsub_rn(zv, L);                                                    \
+        const float q = __fsub_rn(Q[i], L);                                                  \
         Q[i] = q;                                                                            \
         const float a = fabsf(q);                                                            \
-        mn2 = fminf(mn2, fmaxf(mn1, a));                                                     \
-        id = (a < mn1) ? (i) : id;                                                           \
+        mn2 = fmaxf(mn1, fminf(mn2, a));                                                     \
         mn1 = fminf(mn1, a);                                                                 \
         sx ^= __float_as_uint(q);                                                            \
     }
@@ -135,10 +148,16 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
         const uint32_t S = sx & 0x80000000u;
         const uint32_t s1 = __float_as_uint(n1) | S, s2 = __float_as_uint(n2) | S;
         uint32_t nsg = 0;
+        int id = 0;
+        // pass 2: an edge whose |Z_mn| equals the minimum gets the second
+        // minimum (on ties both minima are equal, so any such edge may be the
+        // recorded argmin)
         switch (start) {
 #define P2(i)                                                                                \
-    case i: {                                                                                \
-        const uint32_t ms = (id == (i)) ? s2 : s1;                                           \
+    case i: if constexpr ((i) < DMAX) {                                                                                \
+        const bool at_min = fabsf(Q[i]) == mn1;                                              \
+        const uint32_t ms = at_min ? s2 : s1;                                                \
+        id = at_min ? (i) : id;                                                              \
         const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);                      \
         sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(L))));           \
         nsg = __funnelshift_l(L, nsg, 1);                                                    \
@@ -147,87 +166,117 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
 #undef P2
             default: break;
         }
-        *rs = make_uint4(__float_as_uint(n1), __float_as_uint(n2),
-                         nsg | (static_cast<uint32_t>(id) << 27), 0u);
+        rs[0] = __float_as_uint(n1);
+        rs[1] = __float_as_uint(n2);
+        rs[2] = nsg | (static_cast<uint32_t>(id) << 27);
     }
 }
 
 // FP32 hard decision (eq. 21) and syndrome: true when every check holds.
+template <int DMAX>
 __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t *Zs, int lane) {
     uint32_t bad = 0;
-    const int stride = c.rpl * 32;
     for (int l = 0; l < c.mb; ++l) {
         const uint32_t ri = __ldg(c.rowinfo + l);
-        const int d = ri & 255, e0 = static_cast<int>(ri >> 8);
+        const int d = ri & 255;
         const int start = DMAX - d;
         for (int t = 0; t < c.rpl; ++t) {
             if (lane + 32 * t >= c.z) break;
-            const int vb = (e0 * c.rpl + t) * 32 + lane - start * stride;   // slot i: vb + i * stride
+            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
+            uint32_t off[DMAX];
+            switch (start) {
+#define SA(i) \
+    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
+                LDPC_SLOTS(SA)
+#undef SA
+                default: break;
+            }
             uint32_t par = 0;
             switch (start) {
-#define SY(i) \
-    case i: par ^= (__uint_as_float(lds_u32(Zs, __ldg(c.voff + vb + (i) * stride))) > 0.0f) ? 0u : 1u;
-                LDPC_SLOTS(SY)
-#undef SY
+#define SB(i)                                                                          \
+    case i: if constexpr ((i) < DMAX) {                                                                          \
+        const uint32_t u = lds_u32(Zs, off[i]);                                        \
+        par ^= (u - 1u) | u;   /* bit 31 set iff Z <= 0: negatives, -0 and +0 */       \
+    }
+                LDPC_SLOTS(SB)
+#undef SB
                 default: break;
             }
             bad |= par;
         }
     }
-    return !__any_sync(kFull, bad);
+    return !__any_sync(kFull, bad >> 31);
 }
 
 // ---------------------------------------------------------------------------
-// int8 layer, four frames per word.  Posteriors are held in shared memory in
-// offset form (Z + 128, one byte per frame, 1..255).  The check side works on
-// two's-complement bytes: |Z_mn|, the running minimum and second minimum,
-// the argmin slot and the sign parity, with byte-wise compare masks built by
-// prmt's sign replication.  The saturating additions Z_mn = Z_n - L_mn and
-// Z_n = Z_mn + L_mn run on two 16-bit lanes per word (frames 0, 2 and 1, 3)
-// holding non-negative biased values, clamped with packed u16 min/max.
+// int8 layer, four frames per word.  Posteriors live in shared memory in
+// offset form (Z + 128, one byte per frame, values 1..255) and so does
+// Z_mn inside the row.  The check side works byte-wise: |Z_mn| = |x - 128|
+// (one absolute-difference instruction), the running minimum, second minimum
+// and argmin with compare masks from prmt's sign replication, and the sign
+// parity.  The saturating additions Z_mn = Z_n - L_mn and Z_n = Z_mn + L_mn
+// run on two 16-bit lanes per word (frames 0, 2 and 1, 3) holding
+// non-negative biased values, clamped with packed u16 add-max and min.
 // ---------------------------------------------------------------------------
+template <int DMAX>
 __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *Zs, uint32_t *rows,
                                          int lane, bool norm) {
     const uint32_t ri = __ldg(c.rowinfo + layer);
-    const int d = ri & 255, e0 = static_cast<int>(ri >> 8);
+    const int d = ri & 255;
     const int start = DMAX - d;
-    const int stride = c.rpl * 32;
+    // the sign parity of d offset-form values is that of their negatives
+    // flipped once per edge
+    const uint32_t dpar = (d & 1) ? 0x80808080u : 0u;
     for (int t = 0; t < c.rpl; ++t) {
         const int r = lane + 32 * t;
         if (r >= c.z) break;
-        uint32_t *rs = rows + (layer * c.z + r) * kRowWordsI8;
-        const uint4 st0 = reinterpret_cast<const uint4 *>(rs)[0];
-        const uint4 st1 = reinterpret_cast<const uint4 *>(rs)[1];
-        const uint32_t IDX = st0.z;
-        const uint32_t SG[4] = {st0.w, st1.x, st1.y, st1.z};
+        constexpr int SGW = sign_words(DMAX);
+        uint32_t *rs = rows + (layer * c.z + r) * row_words_i8(DMAX);
+        const uint32_t M1 = rs[0], M2 = rs[1], IDX = rs[2];
+        uint32_t SG[SGW];
+#pragma unroll
+        for (int k = 0; k < SGW; ++k) SG[k] = rs[3 + k];
         // offset-128 bytes of -L_old for the four (sign, magnitude) cases
-        const uint32_t P1c = 0x80808080u - st0.x, P2c = 0x80808080u - st0.y;   // L > 0
-        const uint32_t N1c = 0x80808080u | st0.x, N2c = 0x80808080u | st0.y;   // L < 0
-        const int vb = (e0 * c.rpl + t) * 32 + lane - start * stride;   // slot i: vb + i * stride
+        const uint32_t P1c = 0x80808080u - M1, P2c = 0x80808080u - M2;   // L > 0
+        const uint32_t N1c = 0x80808080u | M1, N2c = 0x80808080u | M2;   // L < 0
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
         uint32_t off[DMAX], Q[DMAX];
+        switch (start) {
+#define A1(i) \
+    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
+            LDPC_SLOTS(A1)
+#undef A1
+            default: break;
+        }
+        switch (start) {
+#define B1(i) \
+    case i: if constexpr ((i) < DMAX) { Q[i] = lds_u32(Zs, off[i]); }
+            LDPC_SLOTS(B1)
+#undef B1
+            default: break;
+        }
         uint32_t mn1 = 0x7F7F7F7Fu, mn2 = 0x7F7F7F7Fu, id = 0, sx = 0;
         switch (start) {
 #define I1(i)                                                                                \
-    case i: {                                                                                \
-        off[i] = __ldg(c.voff + vb + (i) * stride);                                                   \
-        const uint32_t u = lds_u32(Zs, off[i]);                                              \
+    case i: if constexpr ((i) < DMAX) {                                                                                \
+        const uint32_t u = Q[i];                                                             \
         const uint32_t sm = msb_bytes_to_mask(SG[(i) >> 3] << (7 - ((i) & 7)));              \
         const uint32_t nq = nonzero_mask(IDX ^ (0x01010101u * (i)));                         \
         const uint32_t nl = bsel(bsel(P2c, P1c, nq), bsel(N2c, N1c, nq), sm);                \
-        const uint32_t qe = clamp_u16x2(lanes_even(u) + lanes_even(nl), 0x00810081u,         \
-                                        0x017F017Fu);                                        \
-        const uint32_t qo = clamp_u16x2(lanes_odd(u) + lanes_odd(nl), 0x00810081u,           \
-                                        0x017F017Fu);                                        \
-        const uint32_t q = lanes_join(qe, qo);                                               \
-        Q[i] = q;                                                                            \
-        const uint32_t sq = msb_bytes_to_mask(q);                                            \
-        const uint32_t a = (q ^ sq) + (sq & 0x01010101u);                                    \
+        /* (Z + 128) + (128 - L) = Z_mn + 256, clamped to Z_mn in [-127, 127] */             \
+        const uint32_t qe = add_clamp_u16x2(lanes_even(u), lanes_even(nl), 0x00810081u,      \
+                                            0x017F017Fu);                                    \
+        const uint32_t qo = add_clamp_u16x2(lanes_odd(u), lanes_odd(nl), 0x00810081u,        \
+                                            0x017F017Fu);                                    \
+        const uint32_t x = lanes_join(qe, qo) ^ 0x80808080u;   /* offset form of Z_mn */     \
+        Q[i] = x;                                                                            \
+        const uint32_t a = __vabsdiffu4(x, 0x80808080u);       /* |Z_mn| */                  \
         const uint32_t lt = lt_mask7(a, mn1);                                                \
         const uint32_t tmax = bsel(a, mn1, lt);                                              \
         mn1 = bsel(mn1, a, lt);                                                              \
         id = bsel(id, 0x01010101u * (i), lt);                                                \
         mn2 = bsel(mn2, tmax, lt_mask7(tmax, mn2));                                          \
-        sx ^= q;                                                                             \
+        sx ^= x;                                                                             \
     }
             LDPC_SLOTS(I1)
 #undef I1
@@ -235,32 +284,38 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
         }
         const uint32_t n1 = norm ? scale34(mn1) : mn1;
         const uint32_t n2 = norm ? scale34(mn2) : mn2;
-        const uint32_t S = sx & 0x80808080u;
+        const uint32_t S = (sx ^ dpar) & 0x80808080u;   // parity of the negative Z_mn
         // offset-128 bytes of L_new for the four (sign, magnitude) cases
         const uint32_t Lp1 = 0x80808080u | n1, Lp2 = 0x80808080u | n2;       // L > 0
         const uint32_t Ln1 = 0x80808080u - n1, Ln2 = 0x80808080u - n2;       // L < 0
-        uint32_t nsg[4] = {0u, 0u, 0u, 0u};
+        uint32_t nsg[SGW];
+#pragma unroll
+        for (int k = 0; k < SGW; ++k) nsg[k] = 0u;
         switch (start) {
 #define I2(i)                                                                                \
-    case i: {                                                                                \
-        const uint32_t q = Q[i];                                                             \
-        const uint32_t neg = (q ^ S) & 0x80808080u;                                          \
+    case i: if constexpr ((i) < DMAX) {                                                                                \
+        const uint32_t x = Q[i];                                                             \
+        const uint32_t neg = ~(x ^ S) & 0x80808080u;   /* S xor (Z_mn < 0) */                \
         const uint32_t nq = nonzero_mask(id ^ (0x01010101u * (i)));                          \
-        const uint32_t y = bsel(bsel(Lp2, Lp1, nq), bsel(Ln2, Ln1, nq), msb_bytes_to_mask(neg)); \
-        const uint32_t x = q ^ 0x80808080u;                                                  \
-        const uint32_t ze = clamp_u16x2(lanes_even(x) + lanes_even(y) + 0x00800080u,         \
-                                        0x01010101u, 0x01FF01FFu);                           \
-        const uint32_t zo = clamp_u16x2(lanes_odd(x) + lanes_odd(y) + 0x00800080u,           \
-                                        0x01010101u, 0x01FF01FFu);                           \
-        sts_u32(Zs, off[i], lanes_join(ze, zo));                                             \
+        const uint32_t y =                                                                   \
+            bsel(bsel(Lp2, Lp1, nq), bsel(Ln2, Ln1, nq), msb_bytes_to_mask(neg));            \
+        /* (Z_mn + 128) + (L + 128) = Z + 256, clamped to Z in [-127, 127] */                \
+        const uint32_t ze = add_clamp_u16x2(lanes_even(x), lanes_even(y), 0x00810081u,       \
+                                            0x017F017Fu);                                    \
+        const uint32_t zo = add_clamp_u16x2(lanes_odd(x), lanes_odd(y), 0x00810081u,         \
+                                            0x017F017Fu);                                    \
+        sts_u32(Zs, off[i], lanes_join(ze, zo) ^ 0x80808080u);                               \
         nsg[(i) >> 3] |= neg >> (7 - ((i) & 7));                                             \
     }
             LDPC_SLOTS(I2)
 #undef I2
             default: break;
         }
-        reinterpret_cast<uint4 *>(rs)[0] = make_uint4(n1, n2, id, nsg[0]);
-        reinterpret_cast<uint4 *>(rs)[1] = make_uint4(nsg[1], nsg[2], nsg[3], 0u);
+        rs[0] = n1;
+        rs[1] = n2;
+        rs[2] = id;
+#pragma unroll
+        for (int k = 0; k < SGW; ++k) rs[3 + k] = nsg[k];
     }
 }
 
@@ -270,26 +325,35 @@ __device__ __forceinline__ uint32_t hard_bytes_off(uint32_t u) {
 }
 
 // int8 syndrome: bit 7 of byte b set when frame b has an unsatisfied check.
+template <int DMAX>
 __device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint32_t *Zs,
                                                     int lane) {
     uint32_t bad = 0;
-    const int stride = c.rpl * 32;
     for (int l = 0; l < c.mb; ++l) {
         const uint32_t ri = __ldg(c.rowinfo + l);
-        const int d = ri & 255, e0 = static_cast<int>(ri >> 8);
+        const int d = ri & 255;
         const int start = DMAX - d;
         for (int t = 0; t < c.rpl; ++t) {
             if (lane + 32 * t >= c.z) break;
-            const int vb = (e0 * c.rpl + t) * 32 + lane - start * stride;   // slot i: vb + i * stride
-            uint32_t par = 0;
+            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
+            uint32_t off[DMAX];
             switch (start) {
-#define SY(i) \
-    case i: par ^= hard_bytes_off(lds_u32(Zs, __ldg(c.voff + vb + (i) * stride)));
-                LDPC_SLOTS(SY)
-#undef SY
+#define SA(i) \
+    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
+                LDPC_SLOTS(SA)
+#undef SA
                 default: break;
             }
-            bad |= par;
+            uint32_t par = 0;
+            switch (start) {
+#define SB(i) \
+    case i: if constexpr ((i) < DMAX) { par ^= lds_u32(Zs, off[i]) - 0x01010101u; }   /* bytes >= 1: no borrow */
+                LDPC_SLOTS(SB)
+#undef SB
+                default: break;
+            }
+            // bit 7 of (u - 1) is set iff Z >= 1; d terms flip the parity d times
+            bad |= (par ^ ((d & 1) ? 0x80808080u : 0u)) & 0x80808080u;
         }
     }
     return __reduce_or_sync(kFull, bad);
@@ -373,20 +437,22 @@ __device__ __forceinline__ int64_t next_work(unsigned long long *ctr, int64_t ba
 }
 
 // ---------------------------------------------------------------------------
-// Kernels.  Shared memory: [W mbarriers (padded to 16 B)][W per-warp regions];
-// a region holds Z_n (N words, 16-byte aligned: the bulk-copy target) and then
-// the row state of all M rows.
+// Kernels, one warp per block.  Shared memory: [mbarrier (16 B)][Z_n: N
+// words, 16-byte aligned, the bulk-copy target][row state of all M rows].
+// With a single warp the posterior array sits at a fixed shared address, so
+// every access is one load or store at the table offset.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+template <int DMAX>
+__global__ void __launch_bounds__(32)
     decode_f32_kernel(DevCode c, const uint32_t *__restrict__ llr, int64_t frames, DecodeParams p,
                       uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
                       float *__restrict__ post, unsigned long long *work, int region_words,
                       int use_bulk) {
     extern __shared__ __align__(16) uint32_t smem[];
-    const int W = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + warp;
-    uint32_t *Zs = smem + (((2 * W) + 3) & ~3) + warp * region_words;
+    constexpr int W = 1;   // one warp per block: Z_n sits at a fixed shared address
+    const int warp = 0, lane = threadIdx.x & 31;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *Zs = smem + 4;
     uint32_t *rows = Zs + ((c.n + 3) & ~3);
     const bool norm = p.normalise != 0;
     if (use_bulk) {
@@ -411,10 +477,10 @@ __global__ void __launch_bounds__(128)
         int done = p.max_iters;
         for (int k = 1; k <= p.max_iters; ++k) {
             for (int l = 0; l < c.mb; ++l) {
-                layer_f32(c, l, Zs, rows, lane, norm, p.alpha);
+                layer_f32<DMAX>(c, l, Zs, rows, lane, norm, p.alpha);
                 __syncwarp();
             }
-            if (p.early_stop && syndrome_ok_f32(c, Zs, lane)) {
+            if (p.early_stop && syndrome_ok_f32<DMAX>(c, Zs, lane)) {
                 done = k;
                 break;
             }
@@ -425,16 +491,17 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-__global__ void __launch_bounds__(128)
+template <int DMAX>
+__global__ void __launch_bounds__(32)
     decode_i8_kernel(DevCode c, const uint32_t *__restrict__ llr, int64_t frames, DecodeParams p,
                      uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
                      int8_t *__restrict__ post, unsigned long long *work, int region_words,
                      int use_bulk) {
     extern __shared__ __align__(16) uint32_t smem[];
-    const int W = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + warp;
-    uint32_t *Zs = smem + (((2 * W) + 3) & ~3) + warp * region_words;
+    constexpr int W = 1;   // one warp per block: Z_n sits at a fixed shared address
+    const int warp = 0, lane = threadIdx.x & 31;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *Zs = smem + 4;
     uint32_t *rows = Zs + ((c.n + 3) & ~3);
     const bool norm = p.normalise != 0;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
@@ -462,7 +529,7 @@ __global__ void __launch_bounds__(128)
         } else {
             for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i) ^ 0x80808080u;
         }
-        for (int i = lane; i < c.m * kRowWordsI8; i += 32) rows[i] = 0u;
+        for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] = 0u;
         __syncwarp();
     }
     const int64_t dyn_base = 4 * nwarps;   // frames beyond the initial groups
@@ -471,10 +538,10 @@ __global__ void __launch_bounds__(128)
         for (int b = 0; b < 4; ++b) any |= fr[b] >= 0;
         if (!any) break;
         for (int l = 0; l < c.mb; ++l) {
-            layer_i8(c, l, Zs, rows, lane, norm);
+            layer_i8<DMAX>(c, l, Zs, rows, lane, norm);
             __syncwarp();
         }
-        const uint32_t bad = p.early_stop ? syndrome_bad_i8(c, Zs, lane) : 0x80808080u;
+        const uint32_t bad = p.early_stop ? syndrome_bad_i8<DMAX>(c, Zs, lane) : 0x80808080u;
         for (int b = 0; b < 4; ++b) {
             if (fr[b] < 0) continue;
             kb[b] += 1;
@@ -496,40 +563,36 @@ __global__ void __launch_bounds__(128)
             for (int i = lane; i < c.n; i += 32)
                 Zs[i] = prmt(Zs[i], __ldg(src + i) ^ 0x80808080u, sel);
             const uint32_t keep = ~(0xFFu << (8 * b));
-            for (int i = lane; i < c.m * kRowWordsI8; i += 32) rows[i] &= keep;
+            for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] &= keep;
             __syncwarp();
         }
     }
 }
 
-ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr, int64_t frames,
-                          const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
-                          void *d_post, cudaStream_t s) {
-    const bool i8 = dtype == LDPC_I8X4;
-    const int rw = i8 ? kRowWordsI8 : kRowWordsF32;
+template <int DMAX>
+static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, int64_t frames,
+                                   const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
+                                   void *d_post, cudaStream_t s) {
+    const int rw = i8 ? row_words_i8(DMAX) : kRowWordsF32;
     const int region_words = (((c.n + 3) & ~3) + c.m * rw + 3) & ~3;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int W = 4;
-    auto smem_for = [&](int w) { return (((2 * w) + 3) & ~3) * 4 + w * region_words * 4; };
-    while (W > 1 && smem_for(W) > max_optin) --W;
-    const int smem = smem_for(W);
+    const int smem = 16 + region_words * 4;
     if (smem > max_optin)
         return fail(LDPC_ERR_UNSUPPORTED, "decode: code too large for shared memory");
     const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (c.n % 4) == 0;
     const int use_bulk = aligned ? 1 : 0;
-    const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel)
-                          : reinterpret_cast<const void *>(decode_f32_kernel);
+    const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel<DMAX>)
+                          : reinterpret_cast<const void *>(decode_f32_kernel<DMAX>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
     per_sm = std::max(per_sm, 1);
     const int64_t units = i8 ? (frames + 3) / 4 : frames;
-    const int64_t want = (units + W - 1) / W;
     int64_t cap = static_cast<int64_t>(per_sm) * sms;
     // LDPC_DECODE_MAX_BLOCKS caps the persistent grid (for tests of the
     // dynamic frame hand-out on small batches).
@@ -537,21 +600,34 @@ ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr, in
         const long v = std::strtol(env, nullptr, 10);
         if (v > 0) cap = std::min<int64_t>(cap, v);
     }
-    const int grid = static_cast<int>(std::min<int64_t>(want, cap));
+    const int grid = static_cast<int>(std::min<int64_t>(units, cap));
     unsigned long long *work = work_slot(c, s);
     if (!work) return LDPC_ERR_CUDA;
     const DevCode dc = dev_view(c);
     const uint32_t *in = static_cast<const uint32_t *>(d_llr);
     if (i8)
-        decode_i8_kernel<<<grid, W * 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
-                                                    static_cast<int8_t *>(d_post), work,
-                                                    region_words, use_bulk);
+        decode_i8_kernel<DMAX><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
+                                                      static_cast<int8_t *>(d_post), work,
+                                                      region_words, use_bulk);
     else
-        decode_f32_kernel<<<grid, W * 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
-                                                     static_cast<float *>(d_post), work,
-                                                     region_words, use_bulk);
+        decode_f32_kernel<DMAX><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
+                                                       static_cast<float *>(d_post), work,
+                                                       region_words, use_bulk);
     e = cudaGetLastError();
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "decode kernel launch");
+}
+
+ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr, int64_t frames,
+                          const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
+                          void *d_post, cudaStream_t s) {
+    const bool i8 = dtype == LDPC_I8X4;
+    switch (c.dslots) {
+#define L(D) \
+    case D: return launch_decode_t<D>(c, i8, d_llr, frames, p, d_hard, d_iters, d_post, s);
+        LDPC_SLOT_CLASSES(L)
+#undef L
+        default: return fail(LDPC_ERR_UNSUPPORTED, "decode: no kernel for this row degree");
+    }
 }
 
 }  // namespace ldpc

@@ -270,12 +270,13 @@ __global__ void stats_kernel(DevCode c, const uint8_t *__restrict__ info,
         uint32_t bad = 0;
         for (int l = 0; l < c.mb; ++l) {
             const uint32_t ri = c.rowinfo[l];
-            const int d = ri & 255, e0 = ri >> 8;
+            const int d = ri & 255;
             for (int t = 0; t < c.rpl; ++t) {
                 if (lane + 32 * t >= c.z) continue;
                 uint32_t par = 0;
                 for (int e = 0; e < d; ++e) {
-                    const int v = c.voff[((e0 + e) * c.rpl + t) * 32 + lane] >> 2;
+                    const int slot = c.dslots - d + e;
+                    const int v = c.voff[((l * c.rpl + t) * c.dslots + slot) * 32 + lane] >> 2;
                     par ^= (h[v >> 5] >> (v & 31)) & 1u;
                 }
                 bad |= par;

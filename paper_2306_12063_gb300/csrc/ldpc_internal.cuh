@@ -14,6 +14,14 @@ namespace ldpc {
 
 constexpr int kMaxNb = 32;          // block columns (row degree <= nb)
 constexpr int kMaxRowDeg = 27;      // sign bits + 5-bit argmin share one word
+// Decoder kernels are built for these numbers of edge slots per row; a code
+// uses the smallest class that holds its largest row degree.
+#define LDPC_SLOT_CLASSES(X) X(8) X(12) X(16) X(20) X(24) X(27)
+inline int slot_class(int max_deg) {
+    for (int d : {8, 12, 16, 20, 24, 27})
+        if (max_deg <= d) return d;
+    return 0;
+}
 constexpr int kMaxZ = 384;        // 4 N < 65536: byte offsets fit uint16
 constexpr int kMaxIters = 1000;
 
@@ -26,13 +34,14 @@ struct Code {
     int mb = 0, nb = 0, kb = 0, z = 0, n = 0, k = 0, m = 0, y = 0;
     int max_deg = 0, min_deg = 0, n_edges = 0;
     int rpl = 0;                     // row slots per lane: ceil(z / 32)
+    int dslots = 0;                  // edge slots per row in the offset table
     std::vector<int16_t> hbm;        // [mb][nb]
     std::vector<int> layer_off;      // [mb + 1] into the edge list
     std::vector<int> edge_col;       // block column j of each edge (sorted per layer)
     std::vector<int> edge_shift;     // its cyclic shift s
     // device copies
     int16_t *d_hbm = nullptr;        // [mb][nb] (encoder)
-    uint16_t *d_voff = nullptr;      // per-lane variable offsets, see make_voff
+    uint16_t *d_voff = nullptr;      // per-lane variable offsets (see ldpc_code_create)
     uint32_t *d_rowinfo = nullptr;   // [mb] layer degree and first edge
     int *d_status = nullptr;         // device status word
     cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
@@ -51,9 +60,10 @@ struct DevCode {
     int n, k, m, z, mb, nb, kb, y;
     int nwords;        // ceil(n / 32)
     int rpl;           // row slots per lane
+    int dslots;        // edge slots per row in the offset table
     int n_edges;       // block edges (nonzeros of H_bm)
     const int16_t *hbm;
-    const uint16_t *voff;     // [n_edges][rpl][32] variable index of each lane/slot/edge
+    const uint16_t *voff;     // [mb][rpl][dslots][32] byte offset of each edge's variable
     const uint32_t *rowinfo;  // [mb] (first_edge << 8) | degree
     int *status;
 };
@@ -61,7 +71,7 @@ struct DevCode {
 inline DevCode dev_view(const Code &c) {
     DevCode d;
     d.n = c.n; d.k = c.k; d.m = c.m; d.z = c.z; d.mb = c.mb; d.nb = c.nb;
-    d.kb = c.kb; d.y = c.y; d.nwords = (c.n + 31) / 32; d.rpl = c.rpl;
+    d.kb = c.kb; d.y = c.y; d.nwords = (c.n + 31) / 32; d.rpl = c.rpl; d.dslots = c.dslots;
     d.n_edges = c.n_edges; d.hbm = c.d_hbm; d.voff = c.d_voff;
     d.rowinfo = c.d_rowinfo; d.status = c.d_status;
     return d;

@@ -226,7 +226,8 @@ def test_dynamic_frame_handout(ldpc, monkeypatch, dtype, shape_name, frames):
     Eb/N0 so iteration counts vary widely."""
     monkeypatch.setenv("LDPC_DECODE_MAX_BLOCKS", "1")
     s = SHAPES[shape_name]
-    _, _, _, llr, _ = oracle_inputs(s, frames, frame0=999, ebn0=1.0 if dtype == "f32" else 1.5)
+    ebn0 = {"wifi648": 1.5, "wifi1944": 3.5}[shape_name]
+    _, _, _, llr, _ = oracle_inputs(s, frames, frame0=999, ebn0=ebn0)
     want, got = _decode_both(ldpc, s, llr, dtype, 15, True)
     _assert_same(want, got)
     assert want[1].min() < 5 and want[1].max() == 15
