@@ -188,6 +188,35 @@ ldpc_status ldpc_decode_host(const ldpc_code *code, ldpc_dtype dtype,
 ldpc_status ldpc_sync(const ldpc_code *code, cudaStream_t stream,
                       double timeout_s);
 
+/* The decoder of ldpc_decode_layered_minsum for callers that cannot allocate
+ * device memory (no counterpart in the paper: it exists for integration).
+ * Creating a code handle allocates its tables with cudaMalloc; some callers
+ * cannot do that -- code running where the allocator is off limits (a host
+ * callback, a real-time thread with a fixed memory budget, a framework that
+ * owns all device allocations).  This call takes the base matrix itself
+ * (host array, same rules as ldpc_code_create) plus the caller's own
+ * buffers, laid out as for ldpc_decode_layered_minsum, and allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch (the per-lane offset table, the work counter and the status word)
+ * lives in a 64 KiB static device array that each GPU loading the library
+ * holds until the process exits; codes whose offset table,
+ * mb * ceil(z/32) * slots * 64 bytes (slots = 8, 12, 16, 20, 24 or 27, the
+ * smallest that holds the largest row degree), exceeds 65280 bytes are
+ * rejected with LDPC_ERR_UNSUPPORTED.  Each call clears the counter and
+ * status word and rewrites the table on `stream` before decoding.  All calls
+ * on a device share the one array and it keeps the last call's contents, so
+ * calls whose GPU work overlaps (on different streams or from different host
+ * threads) race; serialise them.  Errors are reported as for every call.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture. */
+ldpc_status ldpc_decode_layered_minsum_noalloc(const int16_t *hbm, int mb, int nb, int z,
+                                               ldpc_dtype dtype, const void *d_llr,
+                                               int64_t frames,
+                                               const ldpc_decode_params *params,
+                                               uint32_t *d_hard, int32_t *d_iters,
+                                               void *d_post, cudaStream_t stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *ldpc_last_error(void);
 

@@ -76,6 +76,8 @@ def load(build_if_missing: bool = False):
         "ldpc_decode_host_workspace_bytes": ([vp, i32, i64], sz),
         "ldpc_decode_host": ([vp, i32, vp, i64, P(_Params), vp, vp, vp, sz, i64, vp], i32),
         "ldpc_sync": ([vp, vp, ctypes.c_double], i32),
+        "ldpc_decode_layered_minsum_noalloc": ([vp, i32, i32, i32, i32, vp, i64, P(_Params),
+                                                vp, vp, vp, vp], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():

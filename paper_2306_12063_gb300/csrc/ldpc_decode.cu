@@ -630,4 +630,62 @@ ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr, in
     }
 }
 
+// Launch on a kernel-side code view whose tables, status word and work
+// counter are supplied by the caller (the entry point that allocates
+// nothing keeps them in a static device array).
+template <int DMAX>
+static ldpc_status launch_decode_view_t(const DevCode &dc, bool i8, const void *d_llr,
+                                        int64_t frames, const DecodeParams &p, uint32_t *d_hard,
+                                        int32_t *d_iters, void *d_post,
+                                        unsigned long long *work, cudaStream_t s) {
+    const int rw = i8 ? row_words_i8(DMAX) : kRowWordsF32;
+    const int region_words = (((dc.n + 3) & ~3) + dc.m * rw + 3) & ~3;
+    int dev = 0, sms = 148, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int smem = 16 + region_words * 4;
+    if (smem > max_optin)
+        return fail(LDPC_ERR_UNSUPPORTED, "decode: code too large for shared memory");
+    const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (dc.n % 4) == 0;
+    const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel<DMAX>)
+                          : reinterpret_cast<const void *>(decode_f32_kernel<DMAX>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
+    per_sm = std::max(per_sm, 1);
+    const int64_t units = i8 ? (frames + 3) / 4 : frames;
+    const int grid =
+        static_cast<int>(std::min<int64_t>(units, static_cast<int64_t>(per_sm) * sms));
+    const uint32_t *in = static_cast<const uint32_t *>(d_llr);
+    if (i8)
+        decode_i8_kernel<DMAX><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
+                                                      static_cast<int8_t *>(d_post), work,
+                                                      region_words, aligned ? 1 : 0);
+    else
+        decode_f32_kernel<DMAX><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
+                                                       static_cast<float *>(d_post), work,
+                                                       region_words, aligned ? 1 : 0);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "decode kernel launch");
+}
+
+ldpc_status launch_decode_view(const DevCode &dc, ldpc_dtype dtype, const void *d_llr,
+                               int64_t frames, const DecodeParams &p, uint32_t *d_hard,
+                               int32_t *d_iters, void *d_post, unsigned long long *work,
+                               cudaStream_t s) {
+    const bool i8 = dtype == LDPC_I8X4;
+    switch (dc.dslots) {
+#define L(D)                                                                                 \
+    case D:                                                                                  \
+        return launch_decode_view_t<D>(dc, i8, d_llr, frames, p, d_hard, d_iters, d_post,  \
+                                       work, s);
+        LDPC_SLOT_CLASSES(L)
+#undef L
+        default: return fail(LDPC_ERR_UNSUPPORTED, "decode: no kernel for this row degree");
+    }
+}
+
 }  // namespace ldpc

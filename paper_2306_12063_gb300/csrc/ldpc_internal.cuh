@@ -109,6 +109,13 @@ ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr,
                           int64_t frames, const DecodeParams &p, uint32_t *d_hard,
                           int32_t *d_iters, void *d_post, cudaStream_t s);
 
+// Decode launch on a caller-assembled code view (tables, status word and work
+// counter supplied by the caller); no allocation.
+ldpc_status launch_decode_view(const DevCode &dc, ldpc_dtype dtype, const void *d_llr,
+                               int64_t frames, const DecodeParams &p, uint32_t *d_hard,
+                               int32_t *d_iters, void *d_post, unsigned long long *work,
+                               cudaStream_t s);
+
 }  // namespace ldpc
 
 // ---------------------------------------------------------------------------
