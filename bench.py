@@ -104,14 +104,22 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def kernel_source_digest() -> str:
+    """sha256 (first 16 hex digits) of the decoder kernel sources."""
+    h = hashlib.sha256()
+    for name in ("ldpc_decode.cu", "ldpc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2306_12063_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _profile_traffic(kernel_tag: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (its hash is recorded beside the number)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_2306_12063_gb300", "csrc", "ldpc_decode.cu")
     try:
         txt = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_source_digest()
     except OSError:
         return None
     m = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
@@ -308,7 +316,7 @@ def main():
     roofline = {"bound": "alu", "achieved": ach_tops, "peak": peak_tops, "unit": "Tops/s",
                 "frac": ach_tops / peak_tops,
                 "traffic": _profile_traffic("ldpc_decode_i8_wifi1944"),
-                "kernel": "decode_kernel<true> (int8x4)",
+                "kernel": "decode_i8_kernel<20> (int8, four frames per word)",
                 "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz "
                               "(median SM clock sampled during the timed region)",
                 "hbm_gbs": (len(EBN0) * ((F + 3) // 4) * code.n * 4 +

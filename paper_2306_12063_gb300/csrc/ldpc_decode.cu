@@ -81,17 +81,21 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
     return m - (((m + 0x03030303u) >> 2) & 0x3F3F3F3Fu);
 }
 
-#define LDPC_SLOTS(X)                                                                       \
-    X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) \
-    X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26)
-static_assert(kMaxRowDeg == 27, "slot list must cover kMaxRowDeg slots");
 
 // ---------------------------------------------------------------------------
+// Row processing.  Every row runs all DMAX edge slots as straight-line code
+// (so the compiler can interleave the slots freely); a layer of degree d uses
+// slots DMAX-d .. DMAX-1 and the leading slots read a dummy posterior (word N
+// of the posterior array) whose value leaves the row's minimum, second
+// minimum, sign parity and syndrome unchanged.  Stores are made only for the
+// real slots.
+// ---------------------------------------------------------------------------
+
 // FP32 layer: eq. (22) Z_mn = Z_n - L_mn; eq. (23) new L_mn from the
 // smallest and second smallest |Z_mn| and the product of signs; eq. (20) in
 // single-scan form Z_n = Z_mn + L_mn.  Each float operation is an explicitly
-// rounded intrinsic, so no multiply-add is ever contracted.
-// ---------------------------------------------------------------------------
+// rounded intrinsic, so no multiply-add is ever contracted.  The dummy
+// posterior is +inf: |Z_mn| = +inf is never a minimum and its sign is +.
 template <int DMAX>
 __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t *Zs,
                                           uint32_t *rows, int lane, bool norm, float alpha) {
@@ -108,40 +112,23 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
         const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
         uint32_t off[DMAX];
         float Q[DMAX];
-        // pass 1 in three computed-jump phases so that all loads of the row are
-        // in flight together: offsets, posteriors, then the arithmetic
-        switch (start) {
-#define A1(i) \
-    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
-            LDPC_SLOTS(A1)
-#undef A1
-            default: break;
-        }
-        switch (start) {
-#define B1(i) \
-    case i: if constexpr ((i) < DMAX) { Q[i] = __uint_as_float(lds_u32(Zs, off[i])); }
-            LDPC_SLOTS(B1)
-#undef B1
-            default: break;
-        }
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) Q[i] = __uint_as_float(lds_u32(Zs, off[i]));
         float mn1 = __int_as_float(0x7F800000), mn2 = mn1;
         uint32_t sx = 0;
-        switch (start) {
-#define P1(i)                                                                                \
-    case i: if constexpr ((i) < DMAX) {                                                                                \
-        const float mag = (idx == (i)) ? m2 : m1;                                            \
-        const float L = __uint_as_float(__float_as_uint(mag) |                               \
-                                        ((meta << ((i) + 32 - DMAX)) & 0x80000000u));        \
-        const float q = __fsub_rn(Q[i], L);                                                  \
-        Q[i] = q;                                                                            \
-        const float a = fabsf(q);                                                            \
-        mn2 = fmaxf(mn1, fminf(mn2, a));                                                     \
-        mn1 = fminf(mn1, a);                                                                 \
-        sx ^= __float_as_uint(q);                                                            \
-    }
-            LDPC_SLOTS(P1)
-#undef P1
-            default: break;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const float mag = (idx == i) ? m2 : m1;
+            const float L = __uint_as_float(__float_as_uint(mag) |
+                                            ((meta << (i + 32 - DMAX)) & 0x80000000u));
+            const float q = __fsub_rn(Q[i], L);
+            Q[i] = q;
+            const float a = fabsf(q);
+            mn2 = fmaxf(mn1, fminf(mn2, a));
+            mn1 = fminf(mn1, a);
+            sx ^= __float_as_uint(q);
         }
         const float n1 = norm ? __fmul_rn(alpha, mn1) : mn1;
         const float n2 = norm ? __fmul_rn(alpha, mn2) : mn2;
@@ -149,22 +136,17 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
         const uint32_t s1 = __float_as_uint(n1) | S, s2 = __float_as_uint(n2) | S;
         uint32_t nsg = 0;
         int id = 0;
-        // pass 2: an edge whose |Z_mn| equals the minimum gets the second
-        // minimum (on ties both minima are equal, so any such edge may be the
-        // recorded argmin)
-        switch (start) {
-#define P2(i)                                                                                \
-    case i: if constexpr ((i) < DMAX) {                                                                                \
-        const bool at_min = fabsf(Q[i]) == mn1;                                              \
-        const uint32_t ms = at_min ? s2 : s1;                                                \
-        id = at_min ? (i) : id;                                                              \
-        const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);                      \
-        sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(L))));           \
-        nsg = __funnelshift_l(L, nsg, 1);                                                    \
-    }
-            LDPC_SLOTS(P2)
-#undef P2
-            default: break;
+        // an edge whose |Z_mn| equals the minimum gets the second minimum (on
+        // ties both minima are equal, so any such edge may be the argmin)
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const bool at_min = fabsf(Q[i]) == mn1;
+            const uint32_t ms = at_min ? s2 : s1;
+            id = at_min ? i : id;
+            const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);
+            if (i >= start)
+                sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(L))));
+            nsg = __funnelshift_l(L, nsg, 1);
         }
         rs[0] = __float_as_uint(n1);
         rs[1] = __float_as_uint(n2);
@@ -177,30 +159,17 @@ template <int DMAX>
 __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t *Zs, int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
-        const uint32_t ri = __ldg(c.rowinfo + l);
-        const int d = ri & 255;
-        const int start = DMAX - d;
         for (int t = 0; t < c.rpl; ++t) {
             if (lane + 32 * t >= c.z) break;
             const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
             uint32_t off[DMAX];
-            switch (start) {
-#define SA(i) \
-    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
-                LDPC_SLOTS(SA)
-#undef SA
-                default: break;
-            }
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
             uint32_t par = 0;
-            switch (start) {
-#define SB(i)                                                                          \
-    case i: if constexpr ((i) < DMAX) {                                                                          \
-        const uint32_t u = lds_u32(Zs, off[i]);                                        \
-        par ^= (u - 1u) | u;   /* bit 31 set iff Z <= 0: negatives, -0 and +0 */       \
-    }
-                LDPC_SLOTS(SB)
-#undef SB
-                default: break;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) {
+                const uint32_t u = lds_u32(Zs, off[i]);
+                par ^= (u - 1u) | u;   // bit 31 set iff Z <= 0 (negatives, -0 and +0)
             }
             bad |= par;
         }
@@ -210,27 +179,33 @@ __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t
 
 // ---------------------------------------------------------------------------
 // int8 layer, four frames per word.  Posteriors live in shared memory in
-// offset form (Z + 128, one byte per frame, values 1..255) and so does
-// Z_mn inside the row.  The check side works byte-wise: |Z_mn| = |x - 128|
-// (one absolute-difference instruction), the running minimum, second minimum
-// and argmin with compare masks from prmt's sign replication, and the sign
+// offset form (Z + 128, one byte per frame, values 1..255) and so does Z_mn
+// inside the row.  The check side works byte-wise: |Z_mn| = |x - 128| (one
+// absolute-difference instruction), the running minimum, second minimum and
+// argmin with compare masks from prmt's sign replication, and the sign
 // parity.  The saturating additions Z_mn = Z_n - L_mn and Z_n = Z_mn + L_mn
 // run on two 16-bit lanes per word (frames 0, 2 and 1, 3) holding
-// non-negative biased values, clamped with packed u16 add-max and min.
+// non-negative biased values, clamped with packed u16 add-max and min.  The
+// dummy posterior is +127 and the leading slots' stored message sign is
+// kept negative, so their Z_mn clamps to +127: never below a minimum.
 // ---------------------------------------------------------------------------
 template <int DMAX>
 __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *Zs, uint32_t *rows,
                                          int lane, bool norm) {
+    constexpr int SGW = sign_words(DMAX);
     const uint32_t ri = __ldg(c.rowinfo + layer);
     const int d = ri & 255;
     const int start = DMAX - d;
-    // the sign parity of d offset-form values is that of their negatives
-    // flipped once per edge
-    const uint32_t dpar = (d & 1) ? 0x80808080u : 0u;
+    // sign bits forced on for the leading (unused) slots, per sign word
+    uint32_t pad[SGW];
+#pragma unroll
+    for (int k = 0; k < SGW; ++k) {
+        const int nb = min(max(start - 8 * k, 0), 8);
+        pad[k] = ((1u << nb) - 1u) * 0x01010101u;
+    }
     for (int t = 0; t < c.rpl; ++t) {
         const int r = lane + 32 * t;
         if (r >= c.z) break;
-        constexpr int SGW = sign_words(DMAX);
         uint32_t *rs = rows + (layer * c.z + r) * row_words_i8(DMAX);
         const uint32_t M1 = rs[0], M2 = rs[1], IDX = rs[2];
         uint32_t SG[SGW];
@@ -241,75 +216,56 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
         const uint32_t N1c = 0x80808080u | M1, N2c = 0x80808080u | M2;   // L < 0
         const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
         uint32_t off[DMAX], Q[DMAX];
-        switch (start) {
-#define A1(i) \
-    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
-            LDPC_SLOTS(A1)
-#undef A1
-            default: break;
-        }
-        switch (start) {
-#define B1(i) \
-    case i: if constexpr ((i) < DMAX) { Q[i] = lds_u32(Zs, off[i]); }
-            LDPC_SLOTS(B1)
-#undef B1
-            default: break;
-        }
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) Q[i] = lds_u32(Zs, off[i]);
         uint32_t mn1 = 0x7F7F7F7Fu, mn2 = 0x7F7F7F7Fu, id = 0, sx = 0;
-        switch (start) {
-#define I1(i)                                                                                \
-    case i: if constexpr ((i) < DMAX) {                                                                                \
-        const uint32_t u = Q[i];                                                             \
-        const uint32_t sm = msb_bytes_to_mask(SG[(i) >> 3] << (7 - ((i) & 7)));              \
-        const uint32_t nq = nonzero_mask(IDX ^ (0x01010101u * (i)));                         \
-        const uint32_t nl = bsel(bsel(P2c, P1c, nq), bsel(N2c, N1c, nq), sm);                \
-        /* (Z + 128) + (128 - L) = Z_mn + 256, clamped to Z_mn in [-127, 127] */             \
-        const uint32_t qe = add_clamp_u16x2(lanes_even(u), lanes_even(nl), 0x00810081u,      \
-                                            0x017F017Fu);                                    \
-        const uint32_t qo = add_clamp_u16x2(lanes_odd(u), lanes_odd(nl), 0x00810081u,        \
-                                            0x017F017Fu);                                    \
-        const uint32_t x = lanes_join(qe, qo) ^ 0x80808080u;   /* offset form of Z_mn */     \
-        Q[i] = x;                                                                            \
-        const uint32_t a = __vabsdiffu4(x, 0x80808080u);       /* |Z_mn| */                  \
-        const uint32_t lt = lt_mask7(a, mn1);                                                \
-        const uint32_t tmax = bsel(a, mn1, lt);                                              \
-        mn1 = bsel(mn1, a, lt);                                                              \
-        id = bsel(id, 0x01010101u * (i), lt);                                                \
-        mn2 = bsel(mn2, tmax, lt_mask7(tmax, mn2));                                          \
-        sx ^= x;                                                                             \
-    }
-            LDPC_SLOTS(I1)
-#undef I1
-            default: break;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t u = Q[i];
+            const uint32_t sm = msb_bytes_to_mask(SG[i >> 3] << (7 - (i & 7)));
+            const uint32_t nq = nonzero_mask(IDX ^ (0x01010101u * i));
+            const uint32_t nl = bsel(bsel(P2c, P1c, nq), bsel(N2c, N1c, nq), sm);
+            // (Z + 128) + (128 - L) = Z_mn + 256, clamped to Z_mn in [-127, 127]
+            const uint32_t qe =
+                add_clamp_u16x2(lanes_even(u), lanes_even(nl), 0x00810081u, 0x017F017Fu);
+            const uint32_t qo =
+                add_clamp_u16x2(lanes_odd(u), lanes_odd(nl), 0x00810081u, 0x017F017Fu);
+            const uint32_t x = lanes_join(qe, qo) ^ 0x80808080u;   // offset form of Z_mn
+            Q[i] = x;
+            const uint32_t a = __vabsdiffu4(x, 0x80808080u);       // |Z_mn|
+            const uint32_t lt = lt_mask7(a, mn1);
+            const uint32_t tmax = bsel(a, mn1, lt);
+            mn1 = bsel(mn1, a, lt);
+            id = bsel(id, 0x01010101u * i, lt);
+            mn2 = bsel(mn2, tmax, lt_mask7(tmax, mn2));
+            sx ^= x;
         }
         const uint32_t n1 = norm ? scale34(mn1) : mn1;
         const uint32_t n2 = norm ? scale34(mn2) : mn2;
-        const uint32_t S = (sx ^ dpar) & 0x80808080u;   // parity of the negative Z_mn
+        // offset bytes have bit 7 set for Z_mn >= 0: flip once per slot
+        const uint32_t S = (sx ^ ((DMAX & 1) ? 0x80808080u : 0u)) & 0x80808080u;
         // offset-128 bytes of L_new for the four (sign, magnitude) cases
         const uint32_t Lp1 = 0x80808080u | n1, Lp2 = 0x80808080u | n2;       // L > 0
         const uint32_t Ln1 = 0x80808080u - n1, Ln2 = 0x80808080u - n2;       // L < 0
         uint32_t nsg[SGW];
 #pragma unroll
-        for (int k = 0; k < SGW; ++k) nsg[k] = 0u;
-        switch (start) {
-#define I2(i)                                                                                \
-    case i: if constexpr ((i) < DMAX) {                                                                                \
-        const uint32_t x = Q[i];                                                             \
-        const uint32_t neg = ~(x ^ S) & 0x80808080u;   /* S xor (Z_mn < 0) */                \
-        const uint32_t nq = nonzero_mask(id ^ (0x01010101u * (i)));                          \
-        const uint32_t y =                                                                   \
-            bsel(bsel(Lp2, Lp1, nq), bsel(Ln2, Ln1, nq), msb_bytes_to_mask(neg));            \
-        /* (Z_mn + 128) + (L + 128) = Z + 256, clamped to Z in [-127, 127] */                \
-        const uint32_t ze = add_clamp_u16x2(lanes_even(x), lanes_even(y), 0x00810081u,       \
-                                            0x017F017Fu);                                    \
-        const uint32_t zo = add_clamp_u16x2(lanes_odd(x), lanes_odd(y), 0x00810081u,         \
-                                            0x017F017Fu);                                    \
-        sts_u32(Zs, off[i], lanes_join(ze, zo) ^ 0x80808080u);                               \
-        nsg[(i) >> 3] |= neg >> (7 - ((i) & 7));                                             \
-    }
-            LDPC_SLOTS(I2)
-#undef I2
-            default: break;
+        for (int k = 0; k < SGW; ++k) nsg[k] = pad[k];
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t x = Q[i];
+            const uint32_t neg = ~(x ^ S) & 0x80808080u;   // S xor (Z_mn < 0)
+            const uint32_t nq = nonzero_mask(id ^ (0x01010101u * i));
+            const uint32_t y =
+                bsel(bsel(Lp2, Lp1, nq), bsel(Ln2, Ln1, nq), msb_bytes_to_mask(neg));
+            // (Z_mn + 128) + (L + 128) = Z + 256, clamped to Z in [-127, 127]
+            const uint32_t ze =
+                add_clamp_u16x2(lanes_even(x), lanes_even(y), 0x00810081u, 0x017F017Fu);
+            const uint32_t zo =
+                add_clamp_u16x2(lanes_odd(x), lanes_odd(y), 0x00810081u, 0x017F017Fu);
+            if (i >= start) sts_u32(Zs, off[i], lanes_join(ze, zo) ^ 0x80808080u);
+            nsg[i >> 3] |= neg >> (7 - (i & 7));
         }
         rs[0] = n1;
         rs[1] = n2;
@@ -330,33 +286,22 @@ __device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint
                                                     int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
-        const uint32_t ri = __ldg(c.rowinfo + l);
-        const int d = ri & 255;
-        const int start = DMAX - d;
         for (int t = 0; t < c.rpl; ++t) {
             if (lane + 32 * t >= c.z) break;
             const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
             uint32_t off[DMAX];
-            switch (start) {
-#define SA(i) \
-    case i: if constexpr ((i) < DMAX) { off[i] = __ldg(vrow + (i) * 32); }
-                LDPC_SLOTS(SA)
-#undef SA
-                default: break;
-            }
-            uint32_t par = 0;
-            switch (start) {
-#define SB(i) \
-    case i: if constexpr ((i) < DMAX) { par ^= lds_u32(Zs, off[i]) - 0x01010101u; }   /* bytes >= 1: no borrow */
-                LDPC_SLOTS(SB)
-#undef SB
-                default: break;
-            }
-            // bit 7 of (u - 1) is set iff Z >= 1; d terms flip the parity d times
-            bad |= (par ^ ((d & 1) ? 0x80808080u : 0u)) & 0x80808080u;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+            // bit 7 of (u - 1) is set iff Z >= 1, so each of the DMAX terms (the
+            // dummy +127 ones included) flips the parity of the hard decisions
+            uint32_t par = (DMAX & 1) ? 0x80808080u : 0u;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i)
+                par ^= lds_u32(Zs, off[i]) - 0x01010101u;   // bytes >= 1: no borrow
+            bad |= par;
         }
     }
-    return __reduce_or_sync(kFull, bad);
+    return __reduce_or_sync(kFull, bad & 0x80808080u);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,15 +398,16 @@ __global__ void __launch_bounds__(32)
     const int warp = 0, lane = threadIdx.x & 31;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *Zs = smem + 4;
-    uint32_t *rows = Zs + ((c.n + 3) & ~3);
+    uint32_t *rows = Zs + ((c.n + 4) & ~3);   // Z_n words, then the dummy word n
     const bool norm = p.normalise != 0;
+    if (lane == 0) Zs[c.n] = 0x7F800000u;   // dummy posterior +inf for unused edge slots
     if (use_bulk) {
         if (lane == 0) {
             mbar_init(bar, 1);
             fence_mbar_init();
         }
-        __syncwarp();
     }
+    __syncwarp();
     uint32_t phase = 0;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
     int64_t f = blockIdx.x * static_cast<int64_t>(W) + warp;   // first frame static,
@@ -502,7 +448,7 @@ __global__ void __launch_bounds__(32)
     const int warp = 0, lane = threadIdx.x & 31;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *Zs = smem + 4;
-    uint32_t *rows = Zs + ((c.n + 3) & ~3);
+    uint32_t *rows = Zs + ((c.n + 4) & ~3);   // Z_n words, then the dummy word n
     const bool norm = p.normalise != 0;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
     const int64_t g0 = blockIdx.x * static_cast<int64_t>(W) + warp;
@@ -530,6 +476,7 @@ __global__ void __launch_bounds__(32)
             for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i) ^ 0x80808080u;
         }
         for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] = 0u;
+        if (lane == 0) Zs[c.n] = 0xFFFFFFFFu;   // dummy posterior +127 for unused edge slots
         __syncwarp();
     }
     const int64_t dyn_base = 4 * nwarps;   // frames beyond the initial groups
@@ -574,7 +521,7 @@ static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, in
                                    const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                    void *d_post, cudaStream_t s) {
     const int rw = i8 ? row_words_i8(DMAX) : kRowWordsF32;
-    const int region_words = (((c.n + 3) & ~3) + c.m * rw + 3) & ~3;
+    const int region_words = (((c.n + 4) & ~3) + c.m * rw + 3) & ~3;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -639,7 +586,7 @@ static ldpc_status launch_decode_view_t(const DevCode &dc, bool i8, const void *
                                         int32_t *d_iters, void *d_post,
                                         unsigned long long *work, cudaStream_t s) {
     const int rw = i8 ? row_words_i8(DMAX) : kRowWordsF32;
-    const int region_words = (((dc.n + 3) & ~3) + dc.m * rw + 3) & ~3;
+    const int region_words = (((dc.n + 4) & ~3) + dc.m * rw + 3) & ~3;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
