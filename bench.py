@@ -221,6 +221,7 @@ def main():
     import torch
     import paper_2306_12063_gb300 as ldpc
     from paper_2306_12063_gb300 import _build
+    from paper_2306_12063_gb300.shard import frame_offset, reduce_counters
     from paper_2306_12063_gb300.workload import make_batch
 
     assert torch.cuda.is_available(), "bench.py needs a GPU"
@@ -241,7 +242,7 @@ def main():
     F = args.frames
     batches = []
     for b, eb in enumerate(EBN0):
-        frame0 = (rank * len(EBN0) + b) * F
+        frame0 = frame_offset(rank, b, F, len(EBN0))
         bt = make_batch(code, F, frame0, eb, keep_cw=False)
         if args.no_fp32:
             bt.llr = None
@@ -304,8 +305,10 @@ def main():
     fer = {}
     for i, (eb, bt) in enumerate(zip(EBN0, batches)):
         st = code.frame_stats(bt.info, outs[i][0], outs[i][1], MAX_ITERS).cpu().numpy()
-        fer[str(eb)] = {"fer": float(st[1]) / F, "ber": float(st[0]) / (F * code.k),
-                        "undetected_frames": int(st[2]), "mean_iters": float(st[3]) / F}
+        st = reduce_counters(st)          # summed over ranks (each decodes its own frames)
+        nf = F * ws
+        fer[str(eb)] = {"fer": float(st[1]) / nf, "ber": float(st[0]) / (nf * code.k),
+                        "undetected_frames": int(st[2]), "mean_iters": float(st[3]) / nf}
 
     clk = i8_clk or {}
     mhz = clk.get("sm_mhz") or 2070.0
