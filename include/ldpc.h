@@ -151,6 +151,40 @@ ldpc_status ldpc_decode_layered_minsum(const ldpc_code *code, ldpc_dtype dtype,
                                        uint32_t *d_hard, int32_t *d_iters,
                                        void *d_post, cudaStream_t stream);
 
+/* Learned (neural) normalised min-sum: the FP32 decoder above with the
+ * message of eq. (23) scaled, in iteration k = 1..T, by a trained weight per
+ * nonzero block of H_bm: L_mn = w[k-1][q] * min_{n' != n} |Z_mn'| *
+ * prod sgn Z_mn', where q numbers the nonzero blocks of H_bm row by row in
+ * increasing block column (q = 0 .. nnz(H_bm)-1).  The paper's decoder is
+ * the special case of all weights 1 (eq. 23).  d_weights: device
+ * float[T][nnz(H_bm)]; at most T iterations, with the syndrome stop when
+ * early_stop = 1.  Other arguments and layouts as in
+ * ldpc_decode_layered_minsum with dtype LDPC_F32. */
+ldpc_status ldpc_decode_learned_minsum(const ldpc_code *code, const float *d_llr,
+                                       int64_t frames, const float *d_weights, int T,
+                                       int early_stop, uint32_t *d_hard, int32_t *d_iters,
+                                       float *d_post, cudaStream_t stream);
+
+/* Device workspace bytes of ldpc_decode_learned_fallback for `frames`. */
+size_t ldpc_learned_fallback_workspace_bytes(const ldpc_code *code, int64_t frames);
+
+/* Learned decoding with a plain min-sum fallback: ldpc_decode_learned_minsum
+ * (T iterations, syndrome stop), then every frame whose hard decisions still
+ * violate a parity check (Section 4, step 4) is decoded again from its
+ * channel LLRs by the int8 decoder with `fallback` parameters (channel
+ * quantised as in ldpc_quantize_pack_i8 with quant_scale, quant_clip), and
+ * its outputs replace the learned ones; its d_iters entry becomes T plus the
+ * fallback's count.  *h_fallback_frames receives the number of such frames:
+ * the call reads it back and so waits for the learned pass to finish.
+ * d_workspace: ldpc_learned_fallback_workspace_bytes bytes of device memory. */
+ldpc_status ldpc_decode_learned_fallback(const ldpc_code *code, const float *d_llr,
+                                         int64_t frames, const float *d_weights, int T,
+                                         const ldpc_decode_params *fallback,
+                                         float quant_scale, int quant_clip,
+                                         uint32_t *d_hard, int32_t *d_iters,
+                                         int64_t *h_fallback_frames, void *d_workspace,
+                                         size_t workspace_bytes, cudaStream_t stream);
+
 /* Error counts of decoded frames against the sent info bits (the
  * evaluation of Section 6.1).  d_counters int64[4 + max_iters + 1] is
  * overwritten with: [0] info-bit errors, [1] frame errors (any info bit

@@ -79,6 +79,8 @@ def lib():
                          "ldpc_ref_decode_flooding_f32"):
                 getattr(L, name).argtypes = [vp, vp, i64,
                                              ctypes.POINTER(_Params), vp, vp, vp]
+            L.ldpc_ref_decode_layered_weighted_f32.argtypes = [vp, vp, i64, vp, i32, i32,
+                                                               vp, vp, vp]
             L.ldpc_ref_decode_layered_i8.argtypes = [
                 vp, vp, i64, ctypes.POINTER(_Params), vp, vp, vp,
                 ctypes.POINTER(i64)]
@@ -159,6 +161,23 @@ class RefCode:
         _check(lib().ldpc_ref_decode_layered_f32(
             self._h, _ptr(llr), F, ctypes.byref(p), _ptr(hard), _ptr(iters),
             _ptr(post)), "ldpc_ref_decode_layered_f32")
+        return hard, iters, post
+
+    @property
+    def nnz_blocks(self) -> int:
+        return int((self.hbm >= 0).sum())
+
+    def decode_layered_weighted_f32(self, llr, weights, T=None, early_stop=True,
+                                    want_post=True):
+        """Learned normalised min-sum: weights f32[T][nnz(H_bm)]."""
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        T = w.shape[0] if T is None else int(T)
+        assert w.size >= T * self.nnz_blocks
+        llr, F, hard, iters, post, _ = self._decode(
+            None, llr, np.float32, T, 1.0, False, early_stop, want_post, np.float32)
+        _check(lib().ldpc_ref_decode_layered_weighted_f32(
+            self._h, _ptr(llr), F, _ptr(w), T, int(early_stop), _ptr(hard), _ptr(iters),
+            _ptr(post)), "ldpc_ref_decode_layered_weighted_f32")
         return hard, iters, post
 
     def decode_flooding_f32(self, llr, max_iters=10, alpha=0.75, normalise=True,

@@ -644,3 +644,66 @@ int ldpc_ref_decode_flooding_f32(const ldpc_ref_code *c, const float *llr,
     free(Z0); free(Zn); free(L); free(Lnew); free(Q); free(bits);
     return LDPC_REF_OK;
 }
+
+/* Index of the first nonzero block of H_bm block row i in row-major order. */
+static int block_edge_base(const ldpc_ref_code *c, int i) {
+    int q = 0;
+    for (int a = 0; a < i; a++)
+        for (int j = 0; j < c->nb; j++) q += c->hbm[a * c->nb + j] >= 0;
+    return q;
+}
+
+int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *llr,
+                                         int64_t frames, const float *weights, int T,
+                                         int early_stop, uint32_t *hard, int32_t *iters,
+                                         float *post) {
+    ldpc_ref_params p = {T, 1.0f, 0, early_stop};
+    int st = check_params(c, &p, frames, llr, hard, iters);
+    if (st) return st;
+    if (!weights && frames) return LDPC_REF_ERR_INVALID_ARG;
+    const int n = c->n, nw = (n + 31) / 32;
+    int nnzb = 0;
+    for (int q = 0; q < c->mb * c->nb; q++) nnzb += c->hbm[q] >= 0;
+    float *Zn = (float *)malloc(sizeof(float) * n);
+    float *L = (float *)malloc(sizeof(float) * (c->nnz ? c->nnz : 1));
+    float *Q = (float *)malloc(sizeof(float) * (c->max_deg ? c->max_deg : 1));
+    float *Ln = (float *)malloc(sizeof(float) * (c->max_deg ? c->max_deg : 1));
+    uint8_t *bits = (uint8_t *)malloc(n);
+    if (!Zn || !L || !Q || !Ln || !bits) {
+        free(Zn); free(L); free(Q); free(Ln); free(bits);
+        return LDPC_REF_ERR_NOMEM;
+    }
+    for (int64_t f = 0; f < frames; f++) {
+        for (int v = 0; v < n; v++) Zn[v] = llr[f * (int64_t)n + v];
+        for (int e = 0; e < c->nnz; e++) L[e] = 0.0f;
+        int done = T;
+        for (int k = 1; k <= T; k++) {
+            const float *wk = weights + (size_t)(k - 1) * nnzb;
+            for (int i = 0; i < c->mb; i++) {
+                const int q0 = block_edge_base(c, i);
+                for (int r = 0; r < c->z; r++) {
+                    int row = i * c->z + r;
+                    int b = c->row_start[row];
+                    int d = c->row_start[row + 1] - b;
+                    for (int t = 0; t < d; t++)                       /* eq. (22) */
+                        Q[t] = Zn[c->row_var[b + t]] - L[b + t];
+                    for (int t = 0; t < d; t++)                       /* eq. (23), weighted */
+                        Ln[t] = wk[q0 + t] * minsum_excl_f32(Q, d, t);
+                    for (int t = 0; t < d; t++) {                     /* eq. (20) */
+                        L[b + t] = Ln[t];
+                        Zn[c->row_var[b + t]] = Q[t] + Ln[t];
+                    }
+                }
+            }
+            if (early_stop) {
+                hard_from_f32(Zn, n, hard + f * (int64_t)nw, bits);
+                if (ldpc_ref_syndrome_weight(c, bits) == 0) { done = k; break; }
+            }
+        }
+        hard_from_f32(Zn, n, hard + f * (int64_t)nw, bits);
+        iters[f] = done;
+        if (post) for (int v = 0; v < n; v++) post[f * (int64_t)n + v] = Zn[v];
+    }
+    free(Zn); free(L); free(Q); free(Ln); free(bits);
+    return LDPC_REF_OK;
+}

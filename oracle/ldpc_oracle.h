@@ -104,6 +104,16 @@ int ldpc_ref_decode_layered_i8(const ldpc_ref_code *code, const int8_t *llr,
                                int64_t frames, const ldpc_ref_params *p,
                                uint32_t *hard, int32_t *iters, int8_t *post,
                                int64_t *sat_events);
+/* Learned (neural) normalised min-sum: the layered decoder above with the
+ * message of eq. (23) scaled by one weight per iteration and nonzero block of
+ * H_bm, L_mn = w[k-1][q] * min_{n' != n} |Z_mn'| * prod sgn, where q numbers
+ * the nonzero blocks of H_bm row by row in increasing block column and
+ * k = 1..T.  weights f32[T][nnz(H_bm)]; at most T iterations, syndrome stop
+ * if early_stop.  Outputs as for ldpc_ref_decode_layered_f32. */
+int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *code, const float *llr,
+                                         int64_t frames, const float *weights, int T,
+                                         int early_stop, uint32_t *hard, int32_t *iters,
+                                         float *post);
 /* Flooding min-sum, eq. (18)-(21), FP32: all checks from the previous
  * iteration's variable messages, then all posteriors. */
 int ldpc_ref_decode_flooding_f32(const ldpc_ref_code *code, const float *llr,

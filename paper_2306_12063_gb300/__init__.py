@@ -78,6 +78,10 @@ def load(build_if_missing: bool = False):
         "ldpc_sync": ([vp, vp, ctypes.c_double], i32),
         "ldpc_decode_layered_minsum_noalloc": ([vp, i32, i32, i32, i32, vp, i64, P(_Params),
                                                 vp, vp, vp, vp], i32),
+        "ldpc_decode_learned_minsum": ([vp, vp, i64, vp, i32, i32, vp, vp, vp, vp], i32),
+        "ldpc_learned_fallback_workspace_bytes": ([vp, i64], sz),
+        "ldpc_decode_learned_fallback": ([vp, vp, i64, vp, i32, P(_Params), f32, i32, vp, vp,
+                                          P(i64), vp, sz, vp], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -177,6 +181,54 @@ class Code:
                                                  ctypes.byref(p), _ptr(hard), _ptr(iters),
                                                  _ptr(post), _stream(stream)))
         return hard, iters, post
+
+    @property
+    def nnz_blocks(self) -> int:
+        """Nonzero blocks of H_bm: the number of learned weights per iteration."""
+        return int((self.hbm >= 0).sum())
+
+    def decode_learned(self, llr, weights, early_stop: bool = True, want_post: bool = False,
+                       out=None, stream=None):
+        """Learned normalised min-sum: weights float32[T][nnz_blocks] on the GPU."""
+        torch = _torch()
+        F, T = llr.shape[0], weights.shape[0]
+        if out is None:
+            hard = torch.empty((F, self.nwords), dtype=torch.int32, device=llr.device)
+            iters = torch.empty((F,), dtype=torch.int32, device=llr.device)
+            post = (torch.empty((F, self.n), dtype=torch.float32, device=llr.device)
+                    if want_post else None)
+        else:
+            hard, iters, post = out
+        _check(load().ldpc_decode_learned_minsum(self._h, _ptr(llr), int(F), _ptr(weights),
+                                                 int(T), int(bool(early_stop)), _ptr(hard),
+                                                 _ptr(iters), _ptr(post), _stream(stream)))
+        return hard, iters, post
+
+    def learned_workspace_bytes(self, frames: int) -> int:
+        return int(load().ldpc_learned_fallback_workspace_bytes(self._h, int(frames)))
+
+    def decode_learned_fallback(self, llr, weights, fallback_iters: int = 20,
+                                quant_scale: float = 4.0, quant_clip: int = 63, workspace=None,
+                                out=None, stream=None):
+        """Learned decoding, then int8 plain min-sum on the frames that still
+        fail a parity check.  Returns (hard, iters, number of fallback frames)."""
+        torch = _torch()
+        F, T = llr.shape[0], weights.shape[0]
+        if out is None:
+            hard = torch.empty((F, self.nwords), dtype=torch.int32, device=llr.device)
+            iters = torch.empty((F,), dtype=torch.int32, device=llr.device)
+        else:
+            hard, iters = out
+        if workspace is None:
+            workspace = torch.empty(self.learned_workspace_bytes(F), dtype=torch.uint8,
+                                    device=llr.device)
+        fb = _Params(int(fallback_iters), 0.75, 1, 1)
+        cnt = ctypes.c_int64(0)
+        _check(load().ldpc_decode_learned_fallback(
+            self._h, _ptr(llr), int(F), _ptr(weights), int(T), ctypes.byref(fb),
+            float(quant_scale), int(quant_clip), _ptr(hard), _ptr(iters), ctypes.byref(cnt),
+            _ptr(workspace), int(workspace.numel()), _stream(stream)))
+        return hard, iters, int(cnt.value)
 
     def frame_stats(self, info, hard, iters, max_iters: int, out=None, stream=None):
         """int64[4 + max_iters + 1]: bit errors, frame errors, undetected

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libldpc.so")
-SOURCES = ["ldpc_api.cu", "ldpc_gen.cu", "ldpc_decode.cu", "ldpc_noalloc.cu"]
+SOURCES = ["ldpc_api.cu", "ldpc_gen.cu", "ldpc_decode.cu", "ldpc_noalloc.cu", "ldpc_learned.cu"]
 HEADERS = ["ldpc_internal.cuh", os.path.join("..", "..", "include", "ldpc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -106,9 +106,6 @@ static ldpc_status bind(const Code *c) {
 
 using namespace ldpc;
 
-struct ldpc_code {
-    Code c;
-};
 
 extern "C" {
 

@@ -96,12 +96,30 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 // single-scan form Z_n = Z_mn + L_mn.  Each float operation is an explicitly
 // rounded intrinsic, so no multiply-add is ever contracted.  The dummy
 // posterior is +inf: |Z_mn| = +inf is never a minimum and its sign is +.
-template <int DMAX>
+//
+// WT (learned normalised min-sum): the message of edge q in iteration k is
+// w[k-1][q] times the unscaled magnitude, q numbering the nonzero blocks of
+// H_bm row by row.  The row state then keeps the unscaled minima and the
+// message signs before weighting; wprev / wcur point at the weights of the
+// previous and the current iteration.
+template <int DMAX, bool WT = false>
 __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t *Zs,
-                                          uint32_t *rows, int lane, bool norm, float alpha) {
+                                          uint32_t *rows, int lane, bool norm, float alpha,
+                                          const float *wprev = nullptr,
+                                          const float *wcur = nullptr) {
     const uint32_t ri = __ldg(c.rowinfo + layer);
     const int d = ri & 255;
     const int start = DMAX - d;
+    float wp[WT ? DMAX : 1], wc[WT ? DMAX : 1];
+    if (WT) {
+        const int e0 = static_cast<int>(ri >> 8);   // first block edge of this layer
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const int q = e0 + max(i - start, 0);   // leading unused slots reuse edge e0
+            wp[WT ? i : 0] = __ldg(wprev + q);
+            wc[WT ? i : 0] = __ldg(wcur + q);
+        }
+    }
     for (int t = 0; t < c.rpl; ++t) {
         const int r = lane + 32 * t;
         if (r >= c.z) break;
@@ -121,8 +139,11 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
             const float mag = (idx == i) ? m2 : m1;
-            const float L = __uint_as_float(__float_as_uint(mag) |
-                                            ((meta << (i + 32 - DMAX)) & 0x80000000u));
+            // slot i's sign bit moved to bit 31 (a multiply, so it may issue
+            // on the FMA pipe)
+            const uint32_t sbit = (meta * (1u << (i + 32 - DMAX))) & 0x80000000u;
+            const float L = WT ? __uint_as_float(__float_as_uint(__fmul_rn(wp[WT ? i : 0], mag)) ^ sbit)
+                               : __uint_as_float(__float_as_uint(mag) | sbit);
             const float q = __fsub_rn(Q[i], L);
             Q[i] = q;
             const float a = fabsf(q);
@@ -130,8 +151,8 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
             mn1 = fminf(mn1, a);
             sx ^= __float_as_uint(q);
         }
-        const float n1 = norm ? __fmul_rn(alpha, mn1) : mn1;
-        const float n2 = norm ? __fmul_rn(alpha, mn2) : mn2;
+        const float n1 = (norm && !WT) ? __fmul_rn(alpha, mn1) : mn1;
+        const float n2 = (norm && !WT) ? __fmul_rn(alpha, mn2) : mn2;
         const uint32_t S = sx & 0x80000000u;
         const uint32_t s1 = __float_as_uint(n1) | S, s2 = __float_as_uint(n2) | S;
         uint32_t nsg = 0;
@@ -144,8 +165,13 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
             const uint32_t ms = at_min ? s2 : s1;
             id = at_min ? i : id;
             const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);
+            // learned weights: w * magnitude, then the message sign
+            const uint32_t Lw =
+                WT ? __float_as_uint(__fmul_rn(wc[WT ? i : 0], __uint_as_float(L & 0x7FFFFFFFu))) ^
+                         (L & 0x80000000u)
+                   : L;
             if (i >= start)
-                sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(L))));
+                sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(Lw))));
             nsg = __funnelshift_l(L, nsg, 1);
         }
         rs[0] = __float_as_uint(n1);
@@ -220,7 +246,8 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
         for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) Q[i] = lds_u32(Zs, off[i]);
-        uint32_t mn1 = 0x7F7F7F7Fu, mn2 = 0x7F7F7F7Fu, id = 0, sx = 0;
+        uint32_t A[DMAX];
+        uint32_t mn1 = 0x7F7F7F7Fu, mn2 = 0x7F7F7F7Fu, sx = 0;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
             const uint32_t u = Q[i];
@@ -235,10 +262,10 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
             const uint32_t x = lanes_join(qe, qo) ^ 0x80808080u;   // offset form of Z_mn
             Q[i] = x;
             const uint32_t a = __vabsdiffu4(x, 0x80808080u);       // |Z_mn|
+            A[i] = a;
             const uint32_t lt = lt_mask7(a, mn1);
             const uint32_t tmax = bsel(a, mn1, lt);
             mn1 = bsel(mn1, a, lt);
-            id = bsel(id, 0x01010101u * i, lt);
             mn2 = bsel(mn2, tmax, lt_mask7(tmax, mn2));
             sx ^= x;
         }
@@ -252,20 +279,24 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
         uint32_t nsg[SGW];
 #pragma unroll
         for (int k = 0; k < SGW; ++k) nsg[k] = pad[k];
+        uint32_t id = 0;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
             const uint32_t x = Q[i];
-            const uint32_t neg = ~(x ^ S) & 0x80808080u;   // S xor (Z_mn < 0)
-            const uint32_t nq = nonzero_mask(id ^ (0x01010101u * i));
-            const uint32_t y =
-                bsel(bsel(Lp2, Lp1, nq), bsel(Ln2, Ln1, nq), msb_bytes_to_mask(neg));
+            const uint32_t nm = msb_bytes_to_mask(~(x ^ S));   // 0xFF: L_new < 0 (S xor Z_mn < 0)
+            // |Z_mn| >= min, so min + 128 - |Z_mn| lies in [1, 128] and equals
+            // 128 exactly at the minimum: that edge gets the second minimum (on
+            // ties both minima are equal, so any such edge may be the argmin)
+            const uint32_t at_min = msb_bytes_to_mask(mn1 + 0x80808080u - A[i]);
+            id = bsel(id, 0x01010101u * i, at_min);
+            const uint32_t y = bsel(bsel(Lp1, Lp2, at_min), bsel(Ln1, Ln2, at_min), nm);
             // (Z_mn + 128) + (L + 128) = Z + 256, clamped to Z in [-127, 127]
             const uint32_t ze =
                 add_clamp_u16x2(lanes_even(x), lanes_even(y), 0x00810081u, 0x017F017Fu);
             const uint32_t zo =
                 add_clamp_u16x2(lanes_odd(x), lanes_odd(y), 0x00810081u, 0x017F017Fu);
             if (i >= start) sts_u32(Zs, off[i], lanes_join(ze, zo) ^ 0x80808080u);
-            nsg[i >> 3] |= neg >> (7 - (i & 7));
+            nsg[i >> 3] |= nm & ((1u << (i & 7)) * 0x01010101u);
         }
         rs[0] = n1;
         rs[1] = n2;
@@ -387,7 +418,7 @@ __device__ __forceinline__ int64_t next_work(unsigned long long *ctr, int64_t ba
 // With a single warp the posterior array sits at a fixed shared address, so
 // every access is one load or store at the table offset.
 // ---------------------------------------------------------------------------
-template <int DMAX>
+template <int DMAX, bool WT = false>
 __global__ void __launch_bounds__(32)
     decode_f32_kernel(DevCode c, const uint32_t *__restrict__ llr, int64_t frames, DecodeParams p,
                       uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
@@ -422,8 +453,11 @@ __global__ void __launch_bounds__(32)
         __syncwarp();
         int done = p.max_iters;
         for (int k = 1; k <= p.max_iters; ++k) {
+            const float *wcur = WT ? p.weights + static_cast<size_t>(k - 1) * p.n_edges : nullptr;
+            const float *wprev = WT ? p.weights + static_cast<size_t>(k > 1 ? k - 2 : 0) * p.n_edges
+                                    : nullptr;
             for (int l = 0; l < c.mb; ++l) {
-                layer_f32<DMAX>(c, l, Zs, rows, lane, norm, p.alpha);
+                layer_f32<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev, wcur);
                 __syncwarp();
             }
             if (p.early_stop && syndrome_ok_f32<DMAX>(c, Zs, lane)) {
@@ -571,6 +605,53 @@ ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr, in
     switch (c.dslots) {
 #define L(D) \
     case D: return launch_decode_t<D>(c, i8, d_llr, frames, p, d_hard, d_iters, d_post, s);
+        LDPC_SLOT_CLASSES(L)
+#undef L
+        default: return fail(LDPC_ERR_UNSUPPORTED, "decode: no kernel for this row degree");
+    }
+}
+
+template <int DMAX>
+static ldpc_status launch_learned_t(const Code &c, const float *d_llr, int64_t frames,
+                                   const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
+                                   float *d_post, cudaStream_t s) {
+    const int region_words = (((c.n + 4) & ~3) + c.m * kRowWordsF32 + 3) & ~3;
+    int dev = 0, sms = 148, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int smem = 16 + region_words * 4;
+    if (smem > max_optin)
+        return fail(LDPC_ERR_UNSUPPORTED, "decode: code too large for shared memory");
+    const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (c.n % 4) == 0;
+    const void *kern = reinterpret_cast<const void *>(decode_f32_kernel<DMAX, true>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
+    per_sm = std::max(per_sm, 1);
+    int64_t cap = static_cast<int64_t>(per_sm) * sms;
+    if (const char *env = std::getenv("LDPC_DECODE_MAX_BLOCKS")) {
+        const long v = std::strtol(env, nullptr, 10);
+        if (v > 0) cap = std::min<int64_t>(cap, v);
+    }
+    const int grid = static_cast<int>(std::min<int64_t>(frames, cap));
+    unsigned long long *work = work_slot(c, s);
+    if (!work) return LDPC_ERR_CUDA;
+    decode_f32_kernel<DMAX, true><<<grid, 32, smem, s>>>(
+        dev_view(c), reinterpret_cast<const uint32_t *>(d_llr), frames, p, d_hard, d_iters,
+        d_post, work, region_words, aligned ? 1 : 0);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "learned decode kernel launch");
+}
+
+ldpc_status launch_decode_learned(const Code &c, const float *d_llr, int64_t frames,
+                                  const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
+                                  float *d_post, cudaStream_t s) {
+    switch (c.dslots) {
+#define L(D) \
+    case D: return launch_learned_t<D>(c, d_llr, frames, p, d_hard, d_iters, d_post, s);
         LDPC_SLOT_CLASSES(L)
 #undef L
         default: return fail(LDPC_ERR_UNSUPPORTED, "decode: no kernel for this row degree");

@@ -87,6 +87,10 @@ struct DecodeParams {
     float alpha;
     int normalise;
     int early_stop;
+    // learned normalised min-sum (FP32 only): weights[T][n_edges], T = max_iters;
+    // NULL for the plain / alpha-scaled decoder
+    const float *weights = nullptr;
+    int n_edges = 0;
 };
 
 // Launchers (defined in the .cu files).
@@ -109,6 +113,19 @@ ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr,
                           int64_t frames, const DecodeParams &p, uint32_t *d_hard,
                           int32_t *d_iters, void *d_post, cudaStream_t s);
 
+// Learned normalised min-sum (FP32): per-iteration, per-block-edge weights.
+ldpc_status launch_decode_learned(const Code &c, const float *d_llr, int64_t frames,
+                                  const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
+                                  float *d_post, cudaStream_t s);
+
+// Learned decoding followed by the int8 plain min-sum fallback for the
+// frames that still violate a parity check (ldpc_learned.cu).
+size_t learned_fallback_workspace(const Code &c, int64_t frames);
+ldpc_status learned_fallback(const Code &c, const float *d_llr, int64_t frames,
+                             const DecodeParams &learned, const DecodeParams &fb, float scale,
+                             int clip, uint32_t *d_hard, int32_t *d_iters, int64_t *h_count,
+                             void *d_ws, cudaStream_t s);
+
 // Decode launch on a caller-assembled code view (tables, status word and work
 // counter supplied by the caller); no allocation.
 ldpc_status launch_decode_view(const DevCode &dc, ldpc_dtype dtype, const void *d_llr,
@@ -117,6 +134,11 @@ ldpc_status launch_decode_view(const DevCode &dc, ldpc_dtype dtype, const void *
                                cudaStream_t s);
 
 }  // namespace ldpc
+
+// The opaque handle of the C-ABI.
+struct ldpc_code {
+    ldpc::Code c;
+};
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -1,0 +1,115 @@
+"""Learned normalised min-sum on the GPU against the oracle (bit-exact), and
+the learned-then-int8-fallback pipeline against the same steps done by the
+oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ldpc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2306_12063_gb300 import _build
+    _build.build()
+    import paper_2306_12063_gb300 as m
+    m.load()
+    return m
+
+
+def _inputs(shape, frames, ebn0, frame0=0):
+    rc = oracle.RefCode(shape.hbm, shape.z)
+    info = oracle.gen_info(1, frame0, frames, rc.k)
+    llr = oracle.awgn_llr(rc.encode(info), frame0, 1, synth.ebn0_db_to_sigma(ebn0, rc.k / rc.n))
+    return rc, info, llr
+
+
+def _weights(rc, T, seed, lo=0.4, hi=1.0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(T, rc.nnz_blocks)).astype(np.float32)
+
+
+@pytest.mark.parametrize("shape,T,ebn0,frames", [(synth.wifi_n648_r12(), 8, 2.0, 333),
+                                                 (synth.wifi_n1944_r56(), 6, 4.0, 257),
+                                                 (synth.wimax_mixed_set()[-4], 8, 1.8, 41)],
+                         ids=["wifi648", "wifi1944", "wimax2304"])
+def test_learned_bit_exact(ldpc, shape, T, ebn0, frames):
+    rc, _, llr = _inputs(shape, frames, ebn0)
+    w = _weights(rc, T, 5)
+    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, T, early_stop=True)
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                     early_stop=True, want_post=True)
+    assert (gi.cpu().numpy() == wi).all()
+    assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+    assert (gp.cpu().numpy() == wp).all()
+
+
+def test_learned_negative_and_mixed_weights(ldpc):
+    """Weights of either sign (the sign multiplies the message sign)."""
+    shape = synth.wifi_n648_r12()
+    rc, _, llr = _inputs(shape, 64, 2.5)
+    w = _weights(rc, 5, 9, lo=-0.3, hi=1.2)
+    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, 5, early_stop=False)
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                     early_stop=False, want_post=True)
+    assert (gp.cpu().numpy() == wp).all() and (gi.cpu().numpy() == wi).all()
+
+
+def test_learned_constant_weights_equal_normalised(ldpc):
+    shape = synth.wifi_n1944_r56()
+    rc, _, llr = _inputs(shape, 200, 4.0)
+    code = ldpc.Code(shape.hbm, shape.z)
+    w = torch.full((8, rc.nnz_blocks), 0.75, dtype=torch.float32, device="cuda")
+    x = torch.from_numpy(llr).cuda()
+    a = code.decode_learned(x, w, early_stop=True, want_post=True)
+    b = code.decode(x, max_iters=8, alpha=0.75, normalise=True, early_stop=True, want_post=True)
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+
+
+def test_learned_dynamic_handout(ldpc, monkeypatch):
+    monkeypatch.setenv("LDPC_DECODE_MAX_BLOCKS", "1")
+    shape = synth.wifi_n648_r12()
+    rc, _, llr = _inputs(shape, 150, 1.5, frame0=77)
+    w = _weights(rc, 8, 3)
+    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, 8, early_stop=True)
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                     early_stop=True, want_post=True)
+    assert (gi.cpu().numpy() == wi).all() and (gp.cpu().numpy() == wp).all()
+    assert wi.min() < 4 and wi.max() == 8
+
+
+@pytest.mark.parametrize("shape,T,ebn0", [(synth.wifi_n648_r12(), 4, 1.5),
+                                          (synth.wifi_n1944_r56(), 3, 3.5)],
+                         ids=["wifi648", "wifi1944"])
+def test_learned_fallback_pipeline(ldpc, shape, T, ebn0):
+    """Frames the learned decoder leaves with a nonzero syndrome are decoded
+    again by int8 plain min-sum (20 iterations, (3m)>>2), exactly as the
+    oracle does when it runs the same two steps."""
+    frames = 301
+    rc, _, llr = _inputs(shape, frames, ebn0)
+    w = _weights(rc, T, 11, 0.6, 0.9)
+    wh, wi, _ = rc.decode_layered_weighted_f32(llr, w, T, early_stop=True, want_post=False)
+    bits = oracle.unpack_hard(wh, rc.n)
+    fail = np.array([rc.syndrome_weight(b) != 0 for b in bits])
+    assert 0 < fail.sum() < frames
+    q = oracle.quantize_i8(llr[fail], 4.0, 63)
+    fh, fi, _, _ = rc.decode_layered_i8(q, 20, True, True, want_post=False)
+    wh = wh.copy()
+    wi = wi.copy()
+    wh[fail] = fh
+    wi[fail] = T + fi
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, nfb = code.decode_learned_fallback(torch.from_numpy(llr).cuda(),
+                                               torch.from_numpy(w).cuda(), 20)
+    assert nfb == fail.sum()
+    assert (gi.cpu().numpy() == wi).all()
+    assert (gh.cpu().numpy().view(np.uint32) == wh).all()

@@ -257,3 +257,45 @@ def test_quantizer_rounding_and_clip():
     q = oracle.quantize_i8(x, 4.0, 63)
     # 0.5 -> 0 and 1.5 -> 2 (half to even), 1.2 -> 1, clip at +-63
     assert q.tolist() == [0, 2, 0, -2, 1, 63, -63, 63, -63]
+
+
+def test_weighted_worked_example_layer0(golden_z2):
+    """Per-edge message weights (learned normalised min-sum) on the first
+    layer of the worked example, derived by hand from eq. (23)."""
+    c = synth.tiny_z2_code()
+    rc = oracle.RefCode(c.hbm[:1], 2, require_encodable=False)
+    llr = np.array([golden_z2["llr"]], dtype=np.float32)
+    w = np.array([golden_z2["weighted_layer0_weights"]], dtype=np.float32)
+    _, _, post = rc.decode_layered_weighted_f32(llr, w, 1, early_stop=False)
+    assert post[0].tolist() == golden_z2["weighted_after_layer0"]
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.75, 0.6])
+def test_weighted_constant_equals_normalised(alpha):
+    """Constant weights reduce to the normalised decoder (plain for 1.0)."""
+    c = synth.wifi_n648_r12()
+    rc = oracle.RefCode(c.hbm, c.z)
+    rng = np.random.default_rng(17)
+    llr = rng.normal(0.8, 2.2, size=(6, rc.n)).astype(np.float32)
+    T = 7
+    w = np.full((T, rc.nnz_blocks), alpha, dtype=np.float32)
+    a = rc.decode_layered_weighted_f32(llr, w, T, early_stop=True)
+    b = rc.decode_layered_f32(llr, T, alpha, alpha != 1.0, True)
+    assert all((x == y).all() for x, y in zip(a, b))
+
+
+def test_weighted_weights_are_per_block_and_iteration():
+    """Changing one block's weight in one iteration changes exactly the
+    messages of that block from that iteration on (earlier iterations are
+    unaffected)."""
+    c = synth.wifi_n648_r12()
+    rc = oracle.RefCode(c.hbm, c.z)
+    rng = np.random.default_rng(19)
+    llr = rng.normal(0.5, 2.0, size=(3, rc.n)).astype(np.float32)
+    w = np.full((4, rc.nnz_blocks), 0.75, dtype=np.float32)
+    w2 = w.copy()
+    w2[2, 5] = 0.3
+    p_a = [rc.decode_layered_weighted_f32(llr, w, T, early_stop=False)[2] for T in (2, 3)]
+    p_b = [rc.decode_layered_weighted_f32(llr, w2, T, early_stop=False)[2] for T in (2, 3)]
+    assert (p_a[0] == p_b[0]).all()        # iterations 1-2 identical
+    assert not (p_a[1] == p_b[1]).all()    # iteration 3 differs
