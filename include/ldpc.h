@@ -185,6 +185,77 @@ ldpc_status ldpc_decode_learned_fallback(const ldpc_code *code, const float *d_l
                                          int64_t *h_fallback_frames, void *d_workspace,
                                          size_t workspace_bytes, cudaStream_t stream);
 
+/* ---- Training of the learned weights (the paper has no counterpart: it
+ * decodes with fixed messages; this is the unrolled layered decoder of
+ * Section 4 differentiated in reverse mode). ---- */
+
+/* Training forward: exactly T iterations of ldpc_decode_learned_minsum (no
+ * syndrome stop) on every frame, and its loss
+ *   loss[f] = sum over t = 1..T and n of BCE(sigmoid(-Z_n^(t)), c_n)
+ *           = softplus(-Z) + c Z,
+ * the cross-entropy of each iteration's posterior bit probability against
+ * the sent bit.  Inputs: d_llr float[frames][n]; d_bits uint8[frames][n]
+ * (0/1 code bits); d_weights float[T][nnz(H_bm)] (as in
+ * ldpc_decode_learned_minsum).  Outputs, kept for the backward pass:
+ * d_post float[T][frames][n] = Z^(1..T); d_rows uint32[T-1][frames][m][4],
+ * 16-byte aligned, the compressed row state after iterations 1..T-1
+ * (unscaled smallest and second smallest |Z_mn| as float bits, argmin
+ * edge, message sign bits; may be NULL when T = 1); d_loss float[frames];
+ * d_loss_sum (float[1] or NULL) = loss_scale * sum_f d_loss[f], summed in a
+ * fixed order.  The posteriors equal those of the inference decoder bit for
+ * bit. */
+ldpc_status ldpc_learned_train_forward(const ldpc_code *code, const float *d_llr,
+                                       const uint8_t *d_bits, int64_t frames,
+                                       const float *d_weights, int T, float *d_post,
+                                       uint32_t *d_rows, float *d_loss, float loss_scale,
+                                       float *d_loss_sum, cudaStream_t stream);
+
+/* Device workspace bytes of ldpc_learned_train_backward (one gradient row
+ * per frame: frames * T * nnz(H_bm) floats). */
+size_t ldpc_learned_train_workspace_bytes(const ldpc_code *code, int64_t frames, int T);
+
+/* Training backward: gradients of loss_scale * sum_f loss[f] with respect
+ * to the weights (d_grad_weights float[T][nnz(H_bm)], overwritten; the sum
+ * over frames is taken in a fixed order, so the result is reproducible) and,
+ * if d_grad_llr is not NULL, to the channel LLRs (float[frames][n]).  Takes
+ * the forward's inputs and its d_post / d_rows unchanged.  The derivative of
+ * |x| is sign(x); the smallest |Z_mn| of a row passes its gradient to the
+ * first edge attaining it, the second smallest to the first attaining edge
+ * among the others (one subgradient at exact ties); signs have derivative 0.
+ * Shared memory per frame is 4 (2 n + 2 nnz(H)) bytes, so codes above the
+ * device limit return LDPC_ERR_UNSUPPORTED. */
+ldpc_status ldpc_learned_train_backward(const ldpc_code *code, const float *d_llr,
+                                        const uint8_t *d_bits, int64_t frames,
+                                        const float *d_weights, int T, const float *d_post,
+                                        const uint32_t *d_rows, float loss_scale,
+                                        float *d_grad_weights, float *d_grad_llr,
+                                        void *d_workspace, size_t workspace_bytes,
+                                        cudaStream_t stream);
+
+/* One Adam step (Kingma and Ba, 2015) on count floats, step = 1, 2, ...:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * All four arrays are device memory, updated in place. */
+ldpc_status ldpc_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v,
+                           int64_t count, int step, float lr, float beta1, float beta2,
+                           float eps, cudaStream_t stream);
+
+/* Per-frame noise level for training batches: for frame f = frame0 + i,
+ * Eb/N0 (dB) = lo + (hi - lo) u with u = ((x >> 8) + 1/2) / 2^24, x word 0 of
+ * Philox4x32-10 at counter {0, f mod 2^32, f / 2^32, 0} under key
+ * {seed mod 2^32, (seed / 2^32) ^ 0x534E5253}; then
+ * d_sigma[i] = sqrt(1 / (2 rate 10^(Eb/N0 / 10))), computed in double
+ * precision and rounded to float. */
+ldpc_status ldpc_snr_sigma(uint64_t seed, int64_t frame0, int64_t frames, float ebn0_lo_db,
+                           float ebn0_hi_db, float rate, float *d_sigma, cudaStream_t stream);
+
+/* ldpc_awgn_llr with a noise level per frame: frame i uses
+ * sigma = d_sigma[i] and llr_scale = 2 / sigma^2 (eq. 17; each float
+ * operation rounded once).  d_sigma float[frames], device memory. */
+ldpc_status ldpc_awgn_llr_frames(const uint8_t *d_code, int64_t frame0, int64_t frames,
+                                 int n, uint64_t seed, const float *d_sigma, float *d_llr,
+                                 cudaStream_t stream);
+
 /* Error counts of decoded frames against the sent info bits (the
  * evaluation of Section 6.1).  d_counters int64[4 + max_iters + 1] is
  * overwritten with: [0] info-bit errors, [1] frame errors (any info bit

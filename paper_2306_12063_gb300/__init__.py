@@ -17,7 +17,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["LdpcError", "Code", "load", "gen_info", "awgn_llr", "quantize_pack_i8",
-           "F32", "I8X4", "symbols"]
+           "awgn_llr_frames", "snr_sigma", "adam_step", "F32", "I8X4", "symbols"]
 
 F32 = 0
 I8X4 = 1
@@ -82,6 +82,13 @@ def load(build_if_missing: bool = False):
         "ldpc_learned_fallback_workspace_bytes": ([vp, i64], sz),
         "ldpc_decode_learned_fallback": ([vp, vp, i64, vp, i32, P(_Params), f32, i32, vp, vp,
                                           P(i64), vp, sz, vp], i32),
+        "ldpc_learned_train_forward": ([vp, vp, vp, i64, vp, i32, vp, vp, vp, f32, vp, vp], i32),
+        "ldpc_learned_train_workspace_bytes": ([vp, i64, i32], sz),
+        "ldpc_learned_train_backward": ([vp, vp, vp, i64, vp, i32, vp, vp, f32, vp, vp, vp, sz,
+                                         vp], i32),
+        "ldpc_adam_step": ([vp, vp, vp, vp, i64, i32, f32, f32, f32, f32, vp], i32),
+        "ldpc_snr_sigma": ([u64, i64, i64, f32, f32, f32, vp, vp], i32),
+        "ldpc_awgn_llr_frames": ([vp, i64, i64, i32, u64, vp, vp, vp], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -230,6 +237,52 @@ class Code:
             _ptr(workspace), int(workspace.numel()), _stream(stream)))
         return hard, iters, int(cnt.value)
 
+    def train_forward(self, llr, bits, weights, loss_scale: float = 1.0, out=None,
+                      stream=None):
+        """Training forward (T = weights.shape[0] iterations, no early stop).
+        Returns (post float32[T][F][N], rows int32[T-1][F][M][4], loss
+        float32[F], loss_sum float32[1] = loss_scale * sum(loss))."""
+        torch = _torch()
+        F, T = llr.shape[0], weights.shape[0]
+        dev = llr.device
+        if out is None:
+            post = torch.empty((T, F, self.n), dtype=torch.float32, device=dev)
+            rows = torch.empty((max(T - 1, 0), F, self.m, 4), dtype=torch.int32, device=dev)
+            loss = torch.empty((F,), dtype=torch.float32, device=dev)
+            loss_sum = torch.empty((1,), dtype=torch.float32, device=dev)
+        else:
+            post, rows, loss, loss_sum = out
+        _check(load().ldpc_learned_train_forward(
+            self._h, _ptr(llr), _ptr(bits), int(F), _ptr(weights), int(T), _ptr(post),
+            _ptr(rows) if rows.numel() else None, _ptr(loss), float(loss_scale),
+            _ptr(loss_sum), _stream(stream)))
+        return post, rows, loss, loss_sum
+
+    def train_workspace_bytes(self, frames: int, T: int) -> int:
+        return int(load().ldpc_learned_train_workspace_bytes(self._h, int(frames), int(T)))
+
+    def train_backward(self, llr, bits, weights, post, rows, loss_scale: float = 1.0,
+                       want_llr_grad: bool = False, workspace=None, out=None, stream=None):
+        """Gradients of loss_scale * sum(loss) from the training forward's
+        checkpoints: (d/d weights float32[T][nnz_blocks], d/d llr or None)."""
+        torch = _torch()
+        F, T = llr.shape[0], weights.shape[0]
+        dev = llr.device
+        if out is None:
+            gw = torch.empty((T, self.nnz_blocks), dtype=torch.float32, device=dev)
+            gx = (torch.empty((F, self.n), dtype=torch.float32, device=dev)
+                  if want_llr_grad else None)
+        else:
+            gw, gx = out
+        if workspace is None:
+            workspace = torch.empty(max(self.train_workspace_bytes(F, T), 1), dtype=torch.uint8,
+                                    device=dev)
+        _check(load().ldpc_learned_train_backward(
+            self._h, _ptr(llr), _ptr(bits), int(F), _ptr(weights), int(T), _ptr(post),
+            _ptr(rows) if rows.numel() else None, float(loss_scale), _ptr(gw), _ptr(gx),
+            _ptr(workspace), int(workspace.numel()), _stream(stream)))
+        return gw, gx
+
     def frame_stats(self, info, hard, iters, max_iters: int, out=None, stream=None):
         """int64[4 + max_iters + 1]: bit errors, frame errors, undetected
         errors, iteration sum, iteration histogram."""
@@ -297,3 +350,34 @@ def quantize_pack_i8(llr, scale: float = 4.0, clip: int = 63, out=None, stream=N
     _check(load().ldpc_quantize_pack_i8(_ptr(llr), _ptr(out), int(F), int(n), float(scale),
                                         int(clip), _stream(stream)))
     return out
+
+
+def awgn_llr_frames(cw, frame0: int, seed: int, sigma, out=None, stream=None):
+    """eq. (16)-(17) with a noise level per frame: sigma float32[F] on the GPU."""
+    torch = _torch()
+    F, n = cw.shape
+    if out is None:
+        out = torch.empty((F, n), dtype=torch.float32, device=cw.device)
+    _check(load().ldpc_awgn_llr_frames(_ptr(cw), int(frame0), int(F), int(n), int(seed),
+                                       _ptr(sigma), _ptr(out), _stream(stream)))
+    return out
+
+
+def snr_sigma(seed: int, frame0: int, frames: int, ebn0_lo_db: float, ebn0_hi_db: float,
+              rate: float, device="cuda", out=None, stream=None):
+    """Per-frame noise sigma float32[frames] for Eb/N0 uniform in [lo, hi) dB."""
+    torch = _torch()
+    _bind_device(device)
+    if out is None:
+        out = torch.empty((frames,), dtype=torch.float32, device=device)
+    _check(load().ldpc_snr_sigma(int(seed), int(frame0), int(frames), float(ebn0_lo_db),
+                                 float(ebn0_hi_db), float(rate), _ptr(out), _stream(stream)))
+    return out
+
+
+def adam_step(param, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9,
+              beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    """One in-place Adam update of float32 device tensors."""
+    _check(load().ldpc_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v),
+                                 int(param.numel()), int(step), float(lr), float(beta1),
+                                 float(beta2), float(eps), _stream(stream)))

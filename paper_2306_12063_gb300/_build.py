@@ -1,6 +1,6 @@
 """Builds libldpc.so in-tree with nvcc for sm_103a (GB300).
 
-The three translation units compile in parallel and link into one shared
+The translation units compile in parallel and link into one shared
 library with the CUDA runtime linked statically, so the library loads on any
 machine with the driver and has no run-time dependency on a toolkit path.
 """
@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libldpc.so")
-SOURCES = ["ldpc_api.cu", "ldpc_gen.cu", "ldpc_decode.cu", "ldpc_noalloc.cu", "ldpc_learned.cu"]
+SOURCES = ["ldpc_api.cu", "ldpc_gen.cu", "ldpc_decode.cu", "ldpc_noalloc.cu", "ldpc_learned.cu",
+           "ldpc_train.cu"]
 HEADERS = ["ldpc_internal.cuh", os.path.join("..", "..", "include", "ldpc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -77,6 +77,7 @@ static void release(Code &c) {
     cudaFree(c.d_hbm);
     cudaFree(c.d_voff);
     cudaFree(c.d_rowinfo);
+    cudaFree(c.d_edges);
     cudaFree(c.d_status);
     cudaFree(c.d_work);
     for (auto &s : c.aux)
@@ -201,11 +202,16 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
         rowinfo[i] = (static_cast<uint32_t>(c.layer_off[i]) << 8) |
                      static_cast<uint32_t>(c.layer_off[i + 1] - c.layer_off[i]);
     c.voff_words = voff.size();
+    std::vector<uint32_t> edges(c.n_edges);
+    for (int q = 0; q < c.n_edges; ++q)
+        edges[q] = (static_cast<uint32_t>(c.edge_col[q]) << 16) |
+                   static_cast<uint32_t>(c.edge_shift[q]);
 
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&c.d_hbm, sizeof(int16_t) * mb * nb);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_voff, sizeof(uint16_t) * voff.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_rowinfo, sizeof(uint32_t) * mb);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_edges, sizeof(uint32_t) * c.n_edges);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c.d_work, sizeof(unsigned long long) * kWorkSlots);
     if (e == cudaSuccess)
@@ -215,6 +221,9 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c.d_rowinfo, rowinfo.data(), sizeof(uint32_t) * mb,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c.d_edges, edges.data(), sizeof(uint32_t) * c.n_edges,
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c.d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -277,6 +286,29 @@ ldpc_status ldpc_awgn_llr(const uint8_t *d_code, int64_t frame0, int64_t frames,
     if (!(sigma >= 0.0f) || !(llr_scale == llr_scale))
         return fail(LDPC_ERR_INVALID_ARG, "ldpc_awgn_llr: sigma must be >= 0");
     return launch_awgn(d_code, frame0, frames, n, seed, sigma, llr_scale, d_llr, stream);
+}
+
+ldpc_status ldpc_awgn_llr_frames(const uint8_t *d_code, int64_t frame0, int64_t frames, int n,
+                                 uint64_t seed, const float *d_sigma, float *d_llr,
+                                 cudaStream_t stream) {
+    if (frames < 0 || frame0 < 0 || n < 0)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_awgn_llr_frames: negative size");
+    if (frames == 0 || n == 0) return LDPC_OK;
+    if (!d_code || !d_llr || !d_sigma)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_awgn_llr_frames: NULL buffer");
+    return launch_awgn_frames(d_code, frame0, frames, n, seed, d_sigma, d_llr, stream);
+}
+
+ldpc_status ldpc_snr_sigma(uint64_t seed, int64_t frame0, int64_t frames, float ebn0_lo_db,
+                           float ebn0_hi_db, float rate, float *d_sigma, cudaStream_t stream) {
+    if (frames < 0 || frame0 < 0)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_snr_sigma: negative size");
+    if (!(rate > 0.0f && rate <= 1.0f) || !(ebn0_lo_db <= ebn0_hi_db) ||
+        !(ebn0_lo_db > -100.0f && ebn0_hi_db < 100.0f))
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_snr_sigma: bad rate or Eb/N0 range");
+    if (frames == 0) return LDPC_OK;
+    if (!d_sigma) return fail(LDPC_ERR_INVALID_ARG, "ldpc_snr_sigma: NULL buffer");
+    return launch_snr_sigma(seed, frame0, frames, ebn0_lo_db, ebn0_hi_db, rate, d_sigma, stream);
 }
 
 ldpc_status ldpc_quantize_pack_i8(const float *d_llr, uint32_t *d_q, int64_t frames, int n,

@@ -195,9 +195,12 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float *g0, 
     *g1 = __fmul_rn(r, s);
 }
 
+// sigmas == NULL: every frame uses (sigma, scale); otherwise frame i uses
+// sigma = sigmas[i] and scale = 2 / sigma^2 (eq. 17), each operation rounded
+// once.
 __global__ void awgn_kernel(const uint8_t *__restrict__ cw, int64_t frame0, int64_t frames,
                             int n, uint64_t seed, float sigma, float scale,
-                            float *__restrict__ llr) {
+                            const float *__restrict__ sigmas, float *__restrict__ llr) {
     const int calls = (n + 3) / 4;
     const int64_t total = frames * calls;
     const uint2 key = make_uint2(static_cast<uint32_t>(seed),
@@ -211,6 +214,11 @@ __global__ void awgn_kernel(const uint8_t *__restrict__ cw, int64_t frame0, int6
             make_uint4(static_cast<uint32_t>(c), static_cast<uint32_t>(f),
                        static_cast<uint32_t>(f >> 32), 0u),
             key);
+        float sg = sigma, sc = scale;
+        if (sigmas) {
+            sg = sigmas[i];
+            sc = __fdiv_rn(2.0f, __fmul_rn(sg, sg));
+        }
         float g[4];
         box_muller(w.x, w.y, &g[0], &g[1]);
         box_muller(w.z, w.w, &g[2], &g[3]);
@@ -220,10 +228,31 @@ __global__ void awgn_kernel(const uint8_t *__restrict__ cw, int64_t frame0, int6
             if (p < n) {
                 // eq. (16): x -> 1 - 2x plus noise; eq. (17): llr = 2 y / sigma^2
                 const float x = (cw[i * n + p] & 1u) ? -1.0f : 1.0f;
-                const float y = __fadd_rn(x, __fmul_rn(sigma, g[j]));
-                llr[i * n + p] = __fmul_rn(y, scale);
+                const float y = __fadd_rn(x, __fmul_rn(sg, g[j]));
+                llr[i * n + p] = __fmul_rn(y, sc);
             }
         }
+    }
+}
+
+// Per-frame noise level for training batches: Eb/N0 of frame f uniform in
+// [lo, hi) dB from the top 24 bits of word 0 of Philox4x32-10 at counter
+// {0, f mod 2^32, f / 2^32, 0} under key {seed mod 2^32,
+// (seed / 2^32) ^ 0x534E5253}, u = (bits + 1/2) 2^-24; then
+// sigma^2 = 1 / (2 R 10^(Eb/N0 / 10)) (the BPSK Eb/N0 to noise variance
+// relation), evaluated in double precision and rounded to float.
+__global__ void snr_sigma_kernel(uint64_t seed, int64_t frame0, int64_t frames, double lo,
+                                 double hi, double rate, float *__restrict__ sigma) {
+    const uint2 key = make_uint2(static_cast<uint32_t>(seed),
+                                 static_cast<uint32_t>(seed >> 32) ^ 0x534E5253u);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < frames;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t f = static_cast<uint64_t>(frame0 + i);
+        const uint4 w = philox4x32_10(
+            make_uint4(0u, static_cast<uint32_t>(f), static_cast<uint32_t>(f >> 32), 0u), key);
+        const double u = (static_cast<double>(w.x >> 8) + 0.5) * 0x1p-24;
+        const double ebn0 = lo + (hi - lo) * u;
+        sigma[i] = static_cast<float>(sqrt(1.0 / (2.0 * rate * pow(10.0, ebn0 / 10.0))));
     }
 }
 
@@ -336,9 +365,27 @@ ldpc_status launch_awgn(const uint8_t *d_code, int64_t frame0, int64_t frames, i
                         cudaStream_t s) {
     const int64_t work = frames * ((n + 3) / 4);
     awgn_kernel<<<grid_for(work, 256), 256, 0, s>>>(d_code, frame0, frames, n, seed, sigma,
-                                                    scale, d_llr);
+                                                    scale, nullptr, d_llr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "awgn_kernel");
+}
+
+ldpc_status launch_awgn_frames(const uint8_t *d_code, int64_t frame0, int64_t frames, int n,
+                               uint64_t seed, const float *d_sigma, float *d_llr,
+                               cudaStream_t s) {
+    const int64_t work = frames * ((n + 3) / 4);
+    awgn_kernel<<<grid_for(work, 256), 256, 0, s>>>(d_code, frame0, frames, n, seed, 0.0f, 0.0f,
+                                                    d_sigma, d_llr);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "awgn_kernel");
+}
+
+ldpc_status launch_snr_sigma(uint64_t seed, int64_t frame0, int64_t frames, double lo,
+                             double hi, double rate, float *d_sigma, cudaStream_t s) {
+    snr_sigma_kernel<<<grid_for(frames, 256), 256, 0, s>>>(seed, frame0, frames, lo, hi, rate,
+                                                           d_sigma);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "snr_sigma_kernel");
 }
 
 ldpc_status launch_quantize(const float *d_llr, uint32_t *d_q, int64_t frames, int n,

@@ -43,6 +43,7 @@ struct Code {
     int16_t *d_hbm = nullptr;        // [mb][nb] (encoder)
     uint16_t *d_voff = nullptr;      // per-lane variable offsets (see ldpc_code_create)
     uint32_t *d_rowinfo = nullptr;   // [mb] layer degree and first edge
+    uint32_t *d_edges = nullptr;     // [n_edges] (block column << 16) | shift
     int *d_status = nullptr;         // device status word
     cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -65,6 +66,7 @@ struct DevCode {
     const int16_t *hbm;
     const uint16_t *voff;     // [mb][rpl][dslots][32] byte offset of each edge's variable
     const uint32_t *rowinfo;  // [mb] (first_edge << 8) | degree
+    const uint32_t *edges;    // [n_edges] (block column << 16) | shift
     int *status;
 };
 
@@ -73,7 +75,7 @@ inline DevCode dev_view(const Code &c) {
     d.n = c.n; d.k = c.k; d.m = c.m; d.z = c.z; d.mb = c.mb; d.nb = c.nb;
     d.kb = c.kb; d.y = c.y; d.nwords = (c.n + 31) / 32; d.rpl = c.rpl; d.dslots = c.dslots;
     d.n_edges = c.n_edges; d.hbm = c.d_hbm; d.voff = c.d_voff;
-    d.rowinfo = c.d_rowinfo; d.status = c.d_status;
+    d.rowinfo = c.d_rowinfo; d.edges = c.d_edges; d.status = c.d_status;
     return d;
 }
 
@@ -101,6 +103,11 @@ ldpc_status launch_encode(const Code &c, const uint8_t *d_info, uint8_t *d_code,
 ldpc_status launch_awgn(const uint8_t *d_code, int64_t frame0, int64_t frames, int n,
                         uint64_t seed, float sigma, float scale, float *d_llr,
                         cudaStream_t s);
+ldpc_status launch_awgn_frames(const uint8_t *d_code, int64_t frame0, int64_t frames, int n,
+                               uint64_t seed, const float *d_sigma, float *d_llr,
+                               cudaStream_t s);
+ldpc_status launch_snr_sigma(uint64_t seed, int64_t frame0, int64_t frames, double lo,
+                             double hi, double rate, float *d_sigma, cudaStream_t s);
 ldpc_status launch_quantize(const float *d_llr, uint32_t *d_q, int64_t frames, int n,
                             float scale, int clip, cudaStream_t s);
 ldpc_status launch_stats(const Code &c, const uint8_t *d_info, const uint32_t *d_hard,

@@ -1,0 +1,127 @@
+"""Training of learned normalised min-sum weights with the library's kernels.
+
+The weights w[t][q] scale the eq. (23) message of iteration t on nonzero
+block q of H_bm.  A training step draws a fresh batch from the library's own
+generators (Philox info bits, the direct encoder of eq. (12)-(15), per-frame
+Eb/N0 and the AWGN channel of eq. (16)-(17)), runs the unrolled decoder
+forward with checkpoints, its hand-written backward and an Adam update; the
+loss is the cross-entropy of every iteration's posterior bit probabilities,
+averaged over frames and bits (summed over iterations).  Every step runs in
+libldpc kernels; this module only allocates buffers and sequences calls.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+from . import Code, adam_step, awgn_llr_frames, gen_info, snr_sigma
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def default_iterations(rate: float) -> int:
+    """Unrolled depth: 8 iterations up to rate 2/3, 6 above."""
+    return 8 if rate <= 2.0 / 3.0 + 1e-9 else 6
+
+
+class LearnedMinSumLoss:
+    """torch.autograd.Function: loss = loss_scale * sum over frames of the
+    training loss, differentiable in the weights and the channel LLRs."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, weights, llr, bits, code: Code, loss_scale: float):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, w, x, b, code_, scale):
+                    post, rows, _, loss_sum = code_.train_forward(x, b, w, scale)
+                    ctx.save_for_backward(w, x, b, post, rows)
+                    ctx.code = code_
+                    ctx.scale = scale
+                    return loss_sum.reshape(())
+
+                @staticmethod
+                def backward(ctx, g):
+                    w, x, b, post, rows = ctx.saved_tensors
+                    gw, gx = ctx.code.train_backward(x, b, w, post, rows,
+                                                     ctx.scale * float(g),
+                                                     want_llr_grad=ctx.needs_input_grad[1])
+                    return gw, gx, None, None, None
+
+            cls._fn = _Fn
+        return cls._fn.apply(weights, llr, bits, code, loss_scale)
+
+
+def learned_loss(code: Code, weights, llr, bits, loss_scale: Optional[float] = None):
+    """Differentiable training loss (mean over frames and bits by default)."""
+    if loss_scale is None:
+        loss_scale = 1.0 / (llr.shape[0] * code.n)
+    return LearnedMinSumLoss.apply(weights, llr, bits, code, float(loss_scale))
+
+
+@dataclass
+class TrainConfig:
+    T: int = 8
+    steps: int = 2000
+    batch: int = 4096
+    lr: float = 1e-3
+    ebn0_db: Tuple[float, float] = (1.0, 4.0)
+    seed: int = 1000          # info and noise seed of the training frames
+    init: float = 0.75
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+
+@dataclass
+class TrainResult:
+    weights: object                       # float32[T][nnz_blocks] on the GPU
+    loss_history: object                  # float32[steps] on the GPU
+    config: TrainConfig = field(default_factory=TrainConfig)
+
+
+def train_weights(code: Code, cfg: TrainConfig = TrainConfig(), weights=None,
+                  stream=None) -> TrainResult:
+    """Adam on the learned weights; batch b of step s holds frames
+    s * batch .. (s + 1) * batch - 1 of the training streams."""
+    torch = _torch()
+    dev = code.device
+    B, T, E = cfg.batch, cfg.T, code.nnz_blocks
+    if weights is None:
+        weights = torch.full((T, E), float(cfg.init), dtype=torch.float32, device=dev)
+    m = torch.zeros_like(weights)
+    v = torch.zeros_like(weights)
+    info = torch.empty((B, code.k), dtype=torch.uint8, device=dev)
+    cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
+    sigma = torch.empty((B,), dtype=torch.float32, device=dev)
+    llr = torch.empty((B, code.n), dtype=torch.float32, device=dev)
+    post = torch.empty((T, B, code.n), dtype=torch.float32, device=dev)
+    rows = torch.empty((max(T - 1, 0), B, code.m, 4), dtype=torch.int32, device=dev)
+    loss = torch.empty((B,), dtype=torch.float32, device=dev)
+    hist = torch.empty((cfg.steps,), dtype=torch.float32, device=dev)
+    gw = torch.empty((T, E), dtype=torch.float32, device=dev)
+    ws = torch.empty(max(code.train_workspace_bytes(B, T), 1), dtype=torch.uint8, device=dev)
+    rate = code.k / code.n
+    scale = 1.0 / (B * code.n)
+    for s in range(cfg.steps):
+        f0 = s * B
+        gen_info(cfg.seed, f0, B, code.k, device=dev, out=info, stream=stream)
+        code.encode(info, out=cw, stream=stream)
+        snr_sigma(cfg.seed, f0, B, cfg.ebn0_db[0], cfg.ebn0_db[1], rate, device=dev,
+                  out=sigma, stream=stream)
+        awgn_llr_frames(cw, f0, cfg.seed, sigma, out=llr, stream=stream)
+        code.train_forward(llr, cw, weights, scale, out=(post, rows, loss, hist[s:s + 1]),
+                           stream=stream)
+        code.train_backward(llr, cw, weights, post, rows, scale, workspace=ws, out=(gw, None),
+                            stream=stream)
+        adam_step(weights, gw, m, v, s + 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, stream=stream)
+    return TrainResult(weights, hist, cfg)
