@@ -169,6 +169,105 @@ def run_oracle_sample(frames: int, ebn0: float, threads: int, dtype: str = "i8")
     return frames * rc.k, dt
 
 
+LEARNED_EBN0 = (1.5, 4.5)
+LEARNED_WORKLOAD = ("wifi6-shaped N=648 Z=27 R=1/2 (seeded 12x24 base matrix, seed 0), "
+                    "frames with Eb/N0 uniform in [1.5, 4.5) dB per frame")
+
+
+def learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
+    """Learned normalised min-sum (weights trained at start-up with the
+    library's training kernels, untimed) against plain layered min-sum at 20
+    iterations, decoding the same frames; FER compared with McNemar's test."""
+    from paper_2306_12063_gb300 import stats, train
+    from paper_2306_12063_gb300.shard import reduce_counters
+
+    shape = synth.wifi_n648_r12()
+    code = ldpc.Code(shape.hbm, shape.z, device=dev)
+    rate = code.k / code.n
+    T = train.default_iterations(rate)
+    cfg = train.TrainConfig(T=T)
+    t0 = time.time()
+    tr = train.train_weights(code, cfg)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    hist = tr.loss_history.cpu().numpy()
+    w = tr.weights
+    F = args.learned_frames
+    frame0 = rank * F
+    info = ldpc.gen_info(1, frame0, F, code.k, device=dev)
+    cw = code.encode(info)
+    sig = ldpc.snr_sigma(1, frame0, F, LEARNED_EBN0[0], LEARNED_EBN0[1], rate, device=dev)
+    llr = ldpc.awgn_llr_frames(cw, frame0, 1, sig)
+    del cw
+    q = ldpc.quantize_pack_i8(llr)
+    wsfb = torch.empty(code.learned_workspace_bytes(F), dtype=torch.uint8, device=dev)
+
+    def out():
+        return (torch.empty((F, code.nwords), dtype=torch.int32, device=dev),
+                torch.empty((F,), dtype=torch.int32, device=dev), None)
+
+    outs = {k: out() for k in ("plain_i8_20", "plain_f32_20", "learned", "learned_fallback")}
+    fb_frames = [0]
+
+    def run(name):
+        o = outs[name]
+        if name == "plain_i8_20":
+            code.decode(q, frames=F, dtype=ldpc.I8X4, max_iters=MAX_ITERS, early_stop=True, out=o)
+        elif name == "plain_f32_20":
+            code.decode(llr, dtype=ldpc.F32, max_iters=MAX_ITERS, alpha=0.75, early_stop=True,
+                        out=o)
+        elif name == "learned":
+            code.decode_learned(llr, w, early_stop=True, out=o)
+        else:
+            _, _, fb_frames[0] = code.decode_learned_fallback(llr, w, MAX_ITERS, workspace=wsfb,
+                                                              out=(o[0], o[1]))
+
+    steps = max(1, args.steps // 2)
+    res = {}
+    for name in outs:
+        for _ in range(args.warmup):
+            run(name)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            run(name)
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = a.elapsed_time(b) / steps
+        if pg is not None:
+            tt = torch.tensor([ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            ms = float(tt.item())
+        mi = T + MAX_ITERS if name == "learned_fallback" else (T if name == "learned" else MAX_ITERS)
+        st = reduce_counters(code.frame_stats(info, outs[name][0], outs[name][1], mi).cpu().numpy())
+        nf = F * ws
+        res[name] = {"value": nf * code.k / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms": ms,
+                     "fer": float(st[1]) / nf, "wilson95": stats.wilson_interval(int(st[1]), nf),
+                     "mean_iters": float(st[3]) / nf}
+    res["learned_fallback"]["fallback_frames"] = int(
+        reduce_counters(np.array([fb_frames[0]], dtype=np.int64))[0])
+    comps = {}
+    for plain in ("plain_i8_20", "plain_f32_20"):
+        for lrn in ("learned", "learned_fallback"):
+            cnt = reduce_counters(code.paired_frame_errors(info, outs[lrn][0],
+                                                           outs[plain][0]).cpu().numpy())
+            c = stats.compare(cnt, F * ws)
+            c["speedup"] = res[lrn]["value"] / res[plain]["value"]
+            comps[f"{lrn}_vs_{plain}"] = c
+    return {"workload": LEARNED_WORKLOAD, "frames": F * ws, "T": T,
+            "decoders": res, "comparisons": comps,
+            "matched_fer_test": "exact one-sided McNemar on paired frame outcomes; matched = "
+                                "learned not worse at the 5 % level",
+            "training": {"steps": cfg.steps, "batch": cfg.batch, "lr": cfg.lr,
+                         "ebn0_db": list(cfg.ebn0_db), "init": cfg.init, "seconds": train_s,
+                         "loss_first_100": float(hist[:100].mean()),
+                         "loss_last_100": float(hist[-100:].mean()),
+                         "kernels": "ldpc_learned_train_forward/backward, ldpc_adam_step"}}
+
+
 def reference_arm(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -211,6 +310,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-frames", type=int, default=262144)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -384,6 +485,9 @@ def main():
                sum(int(h.numel()) * 4 for h in h_iters),
                "steps": e_steps, "chunk_frames": chunk,
                "api": "ldpc_decode_host (pinned host buffers, copies inside the timed region)"}
+
+    if not args.no_learned:
+        res["learned"] = learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -267,6 +267,16 @@ ldpc_status ldpc_frame_stats(const ldpc_code *code, const uint8_t *d_info,
                              int64_t frames, int max_iters, int64_t *d_counters,
                              cudaStream_t stream);
 
+/* Paired outcomes of two decoders on the same frames (for the McNemar
+ * comparison of their frame-error rates): d_counts int64[4] is overwritten
+ * with [0] both right, [1] only B wrong, [2] only A wrong, [3] both wrong,
+ * where a frame is wrong when any of its K info bits (the first K hard
+ * decisions) differs from d_info uint8[frames][K].  d_hard_a, d_hard_b as
+ * written by the decoders. */
+ldpc_status ldpc_paired_frame_errors(const ldpc_code *code, const uint8_t *d_info,
+                                     const uint32_t *d_hard_a, const uint32_t *d_hard_b,
+                                     int64_t frames, int64_t *d_counts, cudaStream_t stream);
+
 /* Device bytes that ldpc_decode_host needs as workspace for a given chunk
  * of frames (a multiple of 4). */
 size_t ldpc_decode_host_workspace_bytes(const ldpc_code *code, ldpc_dtype dtype,

@@ -73,6 +73,7 @@ def load(build_if_missing: bool = False):
         "ldpc_quantize_pack_i8": ([vp, vp, i64, i32, f32, i32, vp], i32),
         "ldpc_decode_layered_minsum": ([vp, i32, vp, i64, P(_Params), vp, vp, vp, vp], i32),
         "ldpc_frame_stats": ([vp, vp, vp, vp, i64, i32, vp, vp], i32),
+        "ldpc_paired_frame_errors": ([vp, vp, vp, vp, i64, vp, vp], i32),
         "ldpc_decode_host_workspace_bytes": ([vp, i32, i64], sz),
         "ldpc_decode_host": ([vp, i32, vp, i64, P(_Params), vp, vp, vp, sz, i64, vp], i32),
         "ldpc_sync": ([vp, vp, ctypes.c_double], i32),
@@ -292,6 +293,16 @@ class Code:
         _check(load().ldpc_frame_stats(self._h, _ptr(info), _ptr(hard), _ptr(iters),
                                        int(hard.shape[0]), int(max_iters), _ptr(out),
                                        _stream(stream)))
+        return out
+
+    def paired_frame_errors(self, info, hard_a, hard_b, out=None, stream=None):
+        """int64[4]: frames both right, only B wrong, only A wrong, both wrong."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((4,), dtype=torch.int64, device=hard_a.device)
+        _check(load().ldpc_paired_frame_errors(self._h, _ptr(info), _ptr(hard_a), _ptr(hard_b),
+                                               int(hard_a.shape[0]), _ptr(out),
+                                               _stream(stream)))
         return out
 
     def host_workspace_bytes(self, dtype: int, chunk_frames: int) -> int:

@@ -78,6 +78,7 @@ static void release(Code &c) {
     cudaFree(c.d_voff);
     cudaFree(c.d_rowinfo);
     cudaFree(c.d_edges);
+    cudaFree(c.d_wgather);
     cudaFree(c.d_status);
     cudaFree(c.d_work);
     for (auto &s : c.aux)
@@ -202,6 +203,18 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
         rowinfo[i] = (static_cast<uint32_t>(c.layer_off[i]) << 8) |
                      static_cast<uint32_t>(c.layer_off[i + 1] - c.layer_off[i]);
     c.voff_words = voff.size();
+    // Learned-weight gather table: slot i of layer l (slot order of the
+    // offset table, padded to a multiple of 4) holds block edge
+    // layer_off[l] + i - (D - d), or -1 for a leading unused slot or padding.
+    const int wp = (D + 3) & ~3;
+    std::vector<int16_t> wgather(static_cast<size_t>(mb) * wp, static_cast<int16_t>(-1));
+    for (int i = 0; i < mb; ++i) {
+        const int d = c.layer_off[i + 1] - c.layer_off[i];
+        if (d > D) continue;
+        for (int e = 0; e < d; ++e)
+            wgather[static_cast<size_t>(i) * wp + (D - d + e)] =
+                static_cast<int16_t>(c.layer_off[i] + e);
+    }
     std::vector<uint32_t> edges(c.n_edges);
     for (int q = 0; q < c.n_edges; ++q)
         edges[q] = (static_cast<uint32_t>(c.edge_col[q]) << 16) |
@@ -212,6 +225,7 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     if (e == cudaSuccess) e = cudaMalloc(&c.d_voff, sizeof(uint16_t) * voff.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_rowinfo, sizeof(uint32_t) * mb);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_edges, sizeof(uint32_t) * c.n_edges);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_wgather, sizeof(int16_t) * wgather.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c.d_work, sizeof(unsigned long long) * kWorkSlots);
     if (e == cudaSuccess)
@@ -224,6 +238,9 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c.d_edges, edges.data(), sizeof(uint32_t) * c.n_edges,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c.d_wgather, wgather.data(), sizeof(int16_t) * wgather.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c.d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -381,6 +398,18 @@ ldpc_status ldpc_frame_stats(const ldpc_code *code, const uint8_t *d_info,
     if (st) return st;
     return launch_stats(code->c, d_info, d_hard, d_iters, frames, max_iters, d_counters,
                         stream);
+}
+
+ldpc_status ldpc_paired_frame_errors(const ldpc_code *code, const uint8_t *d_info,
+                                     const uint32_t *d_hard_a, const uint32_t *d_hard_b,
+                                     int64_t frames, int64_t *d_counts, cudaStream_t stream) {
+    if (!code) return fail(LDPC_ERR_INVALID_ARG, "ldpc_paired_frame_errors: code is NULL");
+    if (frames < 0) return fail(LDPC_ERR_INVALID_ARG, "ldpc_paired_frame_errors: frames < 0");
+    if (!d_counts || (frames && (!d_info || !d_hard_a || !d_hard_b)))
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_paired_frame_errors: NULL buffer");
+    ldpc_status st = bind(&code->c);
+    if (st) return st;
+    return launch_paired(code->c, d_info, d_hard_a, d_hard_b, frames, d_counts, stream);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }

@@ -100,8 +100,14 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 // WT (learned normalised min-sum): the message of edge q in iteration k is
 // w[k-1][q] times the unscaled magnitude, q numbering the nonzero blocks of
 // H_bm row by row.  The row state then keeps the unscaled minima and the
-// message signs before weighting; wprev / wcur point at the weights of the
-// previous and the current iteration.
+// message signs before weighting.  wprev / wcur point at this layer's
+// weights of the previous and the current iteration, staged in shared memory
+// in slot order (wpad(DMAX) floats per layer, 16-byte aligned, zero in the
+// leading unused slots).  Since rounding is symmetric in sign,
+// (w |m|) with the sign of m applied afterwards equals w m: one multiply per
+// slot on the signed message.
+__host__ __device__ constexpr int wpad(int dmax) { return (dmax + 3) & ~3; }
+
 template <int DMAX, bool WT = false>
 __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t *Zs,
                                           uint32_t *rows, int lane, bool norm, float alpha,
@@ -110,14 +116,17 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
     const uint32_t ri = __ldg(c.rowinfo + layer);
     const int d = ri & 255;
     const int start = DMAX - d;
-    float wp[WT ? DMAX : 1], wc[WT ? DMAX : 1];
+    float wp[WT ? wpad(DMAX) : 1], wc[WT ? wpad(DMAX) : 1];
     if (WT) {
-        const int e0 = static_cast<int>(ri >> 8);   // first block edge of this layer
+        const float4 *p4 = reinterpret_cast<const float4 *>(wprev);
+        const float4 *c4 = reinterpret_cast<const float4 *>(wcur);
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) {
-            const int q = e0 + max(i - start, 0);   // leading unused slots reuse edge e0
-            wp[WT ? i : 0] = __ldg(wprev + q);
-            wc[WT ? i : 0] = __ldg(wcur + q);
+        for (int j = 0; j < wpad(DMAX) / 4; ++j) {
+            const float4 a = p4[j], b = c4[j];
+            wp[WT ? 4 * j : 0] = a.x; wp[WT ? 4 * j + 1 : 0] = a.y;
+            wp[WT ? 4 * j + 2 : 0] = a.z; wp[WT ? 4 * j + 3 : 0] = a.w;
+            wc[WT ? 4 * j : 0] = b.x; wc[WT ? 4 * j + 1 : 0] = b.y;
+            wc[WT ? 4 * j + 2 : 0] = b.z; wc[WT ? 4 * j + 3 : 0] = b.w;
         }
     }
     for (int t = 0; t < c.rpl; ++t) {
@@ -142,8 +151,8 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
             // slot i's sign bit moved to bit 31 (a multiply, so it may issue
             // on the FMA pipe)
             const uint32_t sbit = (meta * (1u << (i + 32 - DMAX))) & 0x80000000u;
-            const float L = WT ? __uint_as_float(__float_as_uint(__fmul_rn(wp[WT ? i : 0], mag)) ^ sbit)
-                               : __uint_as_float(__float_as_uint(mag) | sbit);
+            const float Lu = __uint_as_float(__float_as_uint(mag) | sbit);
+            const float L = WT ? __fmul_rn(wp[WT ? i : 0], Lu) : Lu;
             const float q = __fsub_rn(Q[i], L);
             Q[i] = q;
             const float a = fabsf(q);
@@ -165,11 +174,9 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
             const uint32_t ms = at_min ? s2 : s1;
             id = at_min ? i : id;
             const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);
-            // learned weights: w * magnitude, then the message sign
-            const uint32_t Lw =
-                WT ? __float_as_uint(__fmul_rn(wc[WT ? i : 0], __uint_as_float(L & 0x7FFFFFFFu))) ^
-                         (L & 0x80000000u)
-                   : L;
+            // learned weights: w times the signed message
+            const uint32_t Lw = WT ? __float_as_uint(__fmul_rn(wc[WT ? i : 0], __uint_as_float(L)))
+                                   : L;
             if (i >= start)
                 sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(Lw))));
             nsg = __funnelshift_l(L, nsg, 1);
@@ -430,6 +437,8 @@ __global__ void __launch_bounds__(32)
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *Zs = smem + 4;
     uint32_t *rows = Zs + ((c.n + 4) & ~3);   // Z_n words, then the dummy word n
+    // learned weights of two iterations, [2][mb][wpad(DMAX)], 16-byte aligned
+    float *wbuf = reinterpret_cast<float *>(rows + ((c.m * kRowWordsF32 + 3) & ~3));
     const bool norm = p.normalise != 0;
     if (lane == 0) Zs[c.n] = 0x7F800000u;   // dummy posterior +inf for unused edge slots
     if (use_bulk) {
@@ -453,11 +462,22 @@ __global__ void __launch_bounds__(32)
         __syncwarp();
         int done = p.max_iters;
         for (int k = 1; k <= p.max_iters; ++k) {
-            const float *wcur = WT ? p.weights + static_cast<size_t>(k - 1) * p.n_edges : nullptr;
-            const float *wprev = WT ? p.weights + static_cast<size_t>(k > 1 ? k - 2 : 0) * p.n_edges
-                                    : nullptr;
+            constexpr int WP = wpad(DMAX);
+            float *wcur = wbuf + (k & 1) * c.mb * WP;
+            const float *wprev = k > 1 ? wbuf + ((k - 1) & 1) * c.mb * WP : wcur;
+            if (WT) {
+                // stage w[k-1] in slot order; iteration 1 also serves as its
+                // own "previous" weights (they multiply zero messages)
+                const float *wk = p.weights + static_cast<size_t>(k - 1) * p.n_edges;
+                for (int i = lane; i < c.mb * WP; i += 32) {
+                    const int g = __ldg(c.wgather + i);
+                    wcur[i] = g >= 0 ? __ldg(wk + g) : 0.0f;
+                }
+                __syncwarp();
+            }
             for (int l = 0; l < c.mb; ++l) {
-                layer_f32<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev, wcur);
+                layer_f32<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
+                                    wcur + l * WP);
                 __syncwarp();
             }
             if (p.early_stop && syndrome_ok_f32<DMAX>(c, Zs, lane)) {
@@ -616,11 +636,11 @@ static ldpc_status launch_learned_t(const Code &c, const float *d_llr, int64_t f
                                    const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                    float *d_post, cudaStream_t s) {
     const int region_words = (((c.n + 4) & ~3) + c.m * kRowWordsF32 + 3) & ~3;
+    const int smem = 16 + (region_words + 2 * c.mb * wpad(DMAX)) * 4;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int smem = 16 + region_words * 4;
     if (smem > max_optin)
         return fail(LDPC_ERR_UNSUPPORTED, "decode: code too large for shared memory");
     const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (c.n % 4) == 0;

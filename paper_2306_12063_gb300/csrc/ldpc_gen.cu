@@ -326,6 +326,28 @@ __global__ void stats_kernel(DevCode c, const uint8_t *__restrict__ info,
     }
 }
 
+// Paired frame outcomes of two decoders on the same frames: cnt[2 a + b]
+// counts the frames where decoder A is wrong (a = 1) or right (a = 0) and
+// decoder B likewise; "wrong" = any info bit differs.  One warp per frame.
+__global__ void paired_kernel(int k, int nwords, const uint8_t *__restrict__ info,
+                              const uint32_t *__restrict__ ha, const uint32_t *__restrict__ hb,
+                              int64_t frames, unsigned long long *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t f = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+         f < frames; f += warps) {
+        const uint8_t *in = info + f * k;
+        uint32_t ea = 0, eb = 0;
+        for (int t = lane; t < k; t += 32) {
+            const uint32_t x = in[t] & 1u;
+            ea |= ((ha[f * nwords + (t >> 5)] >> (t & 31)) & 1u) ^ x;
+            eb |= ((hb[f * nwords + (t >> 5)] >> (t & 31)) & 1u) ^ x;
+        }
+        const bool wa = __any_sync(0xFFFFFFFFu, ea), wb = __any_sync(0xFFFFFFFFu, eb);
+        if (lane == 0) atomicAdd(&cnt[2 * (wa ? 1 : 0) + (wb ? 1 : 0)], 1ull);
+    }
+}
+
 static int grid_for(int64_t work, int threads) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -407,6 +429,19 @@ ldpc_status launch_stats(const Code &c, const uint8_t *d_info, const uint32_t *d
         reinterpret_cast<unsigned long long *>(d_counters));
     e = cudaGetLastError();
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "stats_kernel");
+}
+
+ldpc_status launch_paired(const Code &c, const uint8_t *d_info, const uint32_t *d_hard_a,
+                          const uint32_t *d_hard_b, int64_t frames, int64_t *d_counts,
+                          cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(int64_t) * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counters");
+    if (frames == 0) return LDPC_OK;
+    paired_kernel<<<grid_for(frames * 32, 256), 256, 0, s>>>(
+        c.k, (c.n + 31) / 32, d_info, d_hard_a, d_hard_b, frames,
+        reinterpret_cast<unsigned long long *>(d_counts));
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "paired_kernel");
 }
 
 }  // namespace ldpc

@@ -44,6 +44,7 @@ struct Code {
     uint16_t *d_voff = nullptr;      // per-lane variable offsets (see ldpc_code_create)
     uint32_t *d_rowinfo = nullptr;   // [mb] layer degree and first edge
     uint32_t *d_edges = nullptr;     // [n_edges] (block column << 16) | shift
+    int16_t *d_wgather = nullptr;    // [mb][(dslots + 3) & ~3] block edge of each slot, -1 unused
     int *d_status = nullptr;         // device status word
     cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -67,6 +68,7 @@ struct DevCode {
     const uint16_t *voff;     // [mb][rpl][dslots][32] byte offset of each edge's variable
     const uint32_t *rowinfo;  // [mb] (first_edge << 8) | degree
     const uint32_t *edges;    // [n_edges] (block column << 16) | shift
+    const int16_t *wgather;   // [mb][(dslots + 3) & ~3] block edge of each slot, -1 unused
     int *status;
 };
 
@@ -75,7 +77,7 @@ inline DevCode dev_view(const Code &c) {
     d.n = c.n; d.k = c.k; d.m = c.m; d.z = c.z; d.mb = c.mb; d.nb = c.nb;
     d.kb = c.kb; d.y = c.y; d.nwords = (c.n + 31) / 32; d.rpl = c.rpl; d.dslots = c.dslots;
     d.n_edges = c.n_edges; d.hbm = c.d_hbm; d.voff = c.d_voff;
-    d.rowinfo = c.d_rowinfo; d.edges = c.d_edges; d.status = c.d_status;
+    d.rowinfo = c.d_rowinfo; d.edges = c.d_edges; d.wgather = c.d_wgather; d.status = c.d_status;
     return d;
 }
 
@@ -113,6 +115,9 @@ ldpc_status launch_quantize(const float *d_llr, uint32_t *d_q, int64_t frames, i
 ldpc_status launch_stats(const Code &c, const uint8_t *d_info, const uint32_t *d_hard,
                          const int32_t *d_iters, int64_t frames, int max_iters,
                          int64_t *d_counters, cudaStream_t s);
+ldpc_status launch_paired(const Code &c, const uint8_t *d_info, const uint32_t *d_hard_a,
+                          const uint32_t *d_hard_b, int64_t frames, int64_t *d_counts,
+                          cudaStream_t s);
 // Zeroes the next work-counter slot on stream s and returns it (NULL and an
 // error message on failure).
 unsigned long long *work_slot(const Code &c, cudaStream_t s);

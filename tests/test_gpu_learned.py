@@ -113,3 +113,20 @@ def test_learned_fallback_pipeline(ldpc, shape, T, ebn0):
     assert nfb == fail.sum()
     assert (gi.cpu().numpy() == wi).all()
     assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+
+
+def test_paired_frame_errors(ldpc):
+    """2x2 table of paired frame outcomes against a host count from the
+    unpacked hard decisions."""
+    shape = synth.wifi_n648_r12()
+    rc, info, llr = _inputs(shape, 2000, 1.6)
+    code = ldpc.Code(shape.hbm, shape.z)
+    x = torch.from_numpy(llr).cuda()
+    ha, _, _ = code.decode(x, max_iters=3, early_stop=True)
+    hb, _, _ = code.decode(x, max_iters=20, early_stop=True)
+    cnt = code.paired_frame_errors(torch.from_numpy(info).cuda(), ha, hb).cpu().numpy()
+    wa = (oracle.unpack_hard(ha.cpu().numpy().view(np.uint32), rc.n)[:, :rc.k] != info).any(1)
+    wb = (oracle.unpack_hard(hb.cpu().numpy().view(np.uint32), rc.n)[:, :rc.k] != info).any(1)
+    want = [(~wa & ~wb).sum(), (~wa & wb).sum(), (wa & ~wb).sum(), (wa & wb).sum()]
+    assert cnt.tolist() == [int(v) for v in want]
+    assert want[2] > 0 and want[3] > 0
