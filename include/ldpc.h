@@ -256,6 +256,112 @@ ldpc_status ldpc_awgn_llr_frames(const uint8_t *d_code, int64_t frame0, int64_t 
                                  int n, uint64_t seed, const float *d_sigma, float *d_llr,
                                  cudaStream_t stream);
 
+/* ---- Mixed-code batches (no counterpart in the paper, which decodes one
+ * code per call): frames of several codes decoded together. ---- */
+
+typedef struct ldpc_codeset ldpc_codeset;         /* opaque */
+typedef struct ldpc_mixed_plan ldpc_mixed_plan;   /* opaque */
+typedef struct ldpc_mixed_graph ldpc_mixed_graph; /* opaque */
+
+/* A set of 1..4096 codes (host array of handles, all on one device; the
+ * handles must outlive the set).  The kernel-side descriptor of each code
+ * (sizes and device table pointers) is copied to device memory. */
+ldpc_status ldpc_codeset_create(const ldpc_code *const *codes, int count, ldpc_codeset **out);
+void ldpc_codeset_destroy(ldpc_codeset *set);
+
+/* A batch layout: frame f = 0..frames-1 uses code h_code_of_frame[f] (an
+ * index into the set; host array, copied).  Buffers of a mixed batch hold
+ * the frames back to back in frame order: LLRs (float, or int8 posteriors)
+ * from element llr_off[f] = sum over earlier frames of N, info bits (uint8)
+ * from info_off[f] = sum of K, hard decisions (uint32) from hard_off[f] =
+ * sum of ceil(N/32) words, iteration counts int32[frames].  Internally the
+ * frames are grouped by code (each code's run padded to a multiple of four
+ * frames) and the codes are split into launch groups: one per slot class of
+ * the largest row degree (8, 12, 16, 20, 24, 27), split further so that
+ * shared memory within a group differs by at most a factor of two.  The set
+ * must outlive the plan. */
+ldpc_status ldpc_mixed_plan_create(const ldpc_codeset *set, const int32_t *h_code_of_frame,
+                                   int64_t frames, ldpc_mixed_plan **out);
+void ldpc_mixed_plan_destroy(ldpc_mixed_plan *plan);
+
+/* Buffer sizes of the plan: LLR elements, info bytes, hard-decision words,
+ * packed int8 words (ldpc_mixed_quantize) and the number of launch groups.
+ * Any output pointer may be NULL. */
+ldpc_status ldpc_mixed_plan_sizes(const ldpc_mixed_plan *plan, int64_t *llr_elems,
+                                  int64_t *info_elems, int64_t *hard_words, int64_t *q_words,
+                                  int *launch_groups);
+
+/* The per-frame offsets (host arrays of frames + 1 int64 each, the last
+ * entry the total; any may be NULL). */
+ldpc_status ldpc_mixed_plan_offsets(const ldpc_mixed_plan *plan, int64_t *h_llr_off,
+                                    int64_t *h_info_off, int64_t *h_hard_off);
+
+/* Launch group `group`: slot class, number of codes, shared-memory bytes per
+ * block (FP32 / int8), frames per work item and resident-block cap per SM
+ * (0 = occupancy limit) as currently chosen.  Outputs may be NULL. */
+ldpc_status ldpc_mixed_group_info(const ldpc_mixed_plan *plan, int group, int *slot_class,
+                                  int *codes, int *smem_f32, int *smem_i8, int *chunk_f32,
+                                  int *chunk_i8, int *blocks_per_sm_f32, int *blocks_per_sm_i8);
+
+/* int8 input of a mixed batch: each LLR quantised as in ldpc_quantize_pack_i8
+ * (scale, clip) and packed four frames of the same code per word in the
+ * plan's internal order; padding bytes are +clip.  d_llr float (plan
+ * layout) -> d_q uint32[q_words]. */
+ldpc_status ldpc_mixed_quantize(const ldpc_mixed_plan *plan, const float *d_llr, uint32_t *d_q,
+                                float scale, int clip, cudaStream_t stream);
+
+/* Layered min-sum decoding (as ldpc_decode_layered_minsum, same parameters
+ * for every frame) of a mixed batch: LDPC_F32 reads d_in = LLRs (float, plan
+ * layout; 16-byte aligned with every N a multiple of 4 enables the
+ * bulk-copy path), LDPC_I8X4 reads the words of ldpc_mixed_quantize.  Each
+ * launch group is one persistent kernel launch whose warps take work items
+ * (runs of consecutive frames of one code, largest codes first) from an
+ * atomic counter; the groups' launches are forked from `stream` onto the
+ * plan's own streams and joined back, so later work on `stream` sees the
+ * results.  d_hard, d_iters, d_post (NULL, or float / int8 at llr_off) in
+ * the plan layout.  Calls on one plan must not overlap in time. */
+ldpc_status ldpc_decode_mixed(ldpc_mixed_plan *plan, ldpc_dtype dtype, const void *d_in,
+                              const ldpc_decode_params *params, uint32_t *d_hard,
+                              int32_t *d_iters, void *d_post, cudaStream_t stream);
+
+/* Error counts of a decoded mixed batch: d_counters int64[5 + max_iters] as
+ * in ldpc_frame_stats over all frames; d_code_frame_errors (NULL or
+ * int64[set size]) receives the frame errors per code of the set. */
+ldpc_status ldpc_mixed_stats(const ldpc_mixed_plan *plan, const uint8_t *d_info,
+                             const uint32_t *d_hard, const int32_t *d_iters, int max_iters,
+                             int64_t *d_counters, int64_t *d_code_frame_errors,
+                             cudaStream_t stream);
+
+/* Autotuner: for each launch group in turn, picks the frames per work item
+ * (FP32 1..32, int8 4..128) and then a resident-block cap per SM (none, 16,
+ * 8, 4) that minimise the median time of `reps` decodes of this batch, the
+ * other groups' choices held fixed.  Runs and synchronises `stream`; the
+ * choices stay in the plan (ldpc_mixed_group_info reports them). */
+ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const void *d_in,
+                                const ldpc_decode_params *params, uint32_t *d_hard,
+                                int32_t *d_iters, int reps, cudaStream_t stream);
+
+/* Assembly of a mixed batch from per-code buffers: the rows of code
+ * `code`'s frames, stored consecutively in d_src in batch order, are copied
+ * to their places in the plan layout of d_dst.  what = 0: float LLR rows
+ * (N floats, at llr_off); 1: info bits (K bytes, at info_off); 2: code bits
+ * (N bytes, at llr_off counted in bytes). */
+ldpc_status ldpc_mixed_scatter(const ldpc_mixed_plan *plan, int code, int what,
+                               const void *d_src, void *d_dst, cudaStream_t stream);
+
+/* A CUDA graph of one whole step on fixed buffers: [LDPC_I8X4: quantise
+ * d_llr into d_q] -> the decode launches of every group (parallel branches)
+ * -> [if d_counters: ldpc_mixed_stats against d_info with max_iters =
+ * params->max_iters].  Captured from the plan's current choices; replay with
+ * ldpc_mixed_graph_launch.  The plan and the buffers must outlive it. */
+ldpc_status ldpc_mixed_graph_create(ldpc_mixed_plan *plan, ldpc_dtype dtype, const float *d_llr,
+                                    uint32_t *d_q, float quant_scale, int quant_clip,
+                                    const ldpc_decode_params *params, uint32_t *d_hard,
+                                    int32_t *d_iters, const uint8_t *d_info, int64_t *d_counters,
+                                    int64_t *d_code_frame_errors, ldpc_mixed_graph **out);
+ldpc_status ldpc_mixed_graph_launch(ldpc_mixed_graph *graph, cudaStream_t stream);
+void ldpc_mixed_graph_destroy(ldpc_mixed_graph *graph);
+
 /* Error counts of decoded frames against the sent info bits (the
  * evaluation of Section 6.1).  d_counters int64[4 + max_iters + 1] is
  * overwritten with: [0] info-bit errors, [1] frame errors (any info bit

@@ -17,7 +17,8 @@ import numpy as np
 from . import _build
 
 __all__ = ["LdpcError", "Code", "load", "gen_info", "awgn_llr", "quantize_pack_i8",
-           "awgn_llr_frames", "snr_sigma", "adam_step", "F32", "I8X4", "symbols"]
+           "awgn_llr_frames", "snr_sigma", "adam_step", "CodeSet", "MixedPlan", "MixedGraph",
+           "F32", "I8X4", "symbols"]
 
 F32 = 0
 I8X4 = 1
@@ -90,6 +91,22 @@ def load(build_if_missing: bool = False):
         "ldpc_adam_step": ([vp, vp, vp, vp, i64, i32, f32, f32, f32, f32, vp], i32),
         "ldpc_snr_sigma": ([u64, i64, i64, f32, f32, f32, vp, vp], i32),
         "ldpc_awgn_llr_frames": ([vp, i64, i64, i32, u64, vp, vp, vp], i32),
+        "ldpc_codeset_create": ([vp, i32, P(vp)], i32),
+        "ldpc_codeset_destroy": ([vp], None),
+        "ldpc_mixed_plan_create": ([vp, vp, i64, P(vp)], i32),
+        "ldpc_mixed_plan_destroy": ([vp], None),
+        "ldpc_mixed_plan_sizes": ([vp, P(i64), P(i64), P(i64), P(i64), P(i32)], i32),
+        "ldpc_mixed_plan_offsets": ([vp, vp, vp, vp], i32),
+        "ldpc_mixed_group_info": ([vp, i32] + [P(i32)] * 8, i32),
+        "ldpc_mixed_quantize": ([vp, vp, vp, f32, i32, vp], i32),
+        "ldpc_decode_mixed": ([vp, i32, vp, P(_Params), vp, vp, vp, vp], i32),
+        "ldpc_mixed_stats": ([vp, vp, vp, vp, i32, vp, vp, vp], i32),
+        "ldpc_mixed_autotune": ([vp, i32, vp, P(_Params), vp, vp, i32, vp], i32),
+        "ldpc_mixed_scatter": ([vp, i32, i32, vp, vp, vp], i32),
+        "ldpc_mixed_graph_create": ([vp, i32, vp, vp, f32, i32, P(_Params), vp, vp, vp, vp, vp,
+                                     P(vp)], i32),
+        "ldpc_mixed_graph_launch": ([vp, vp], i32),
+        "ldpc_mixed_graph_destroy": ([vp], None),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -322,6 +339,155 @@ class Code:
 
     def sync(self, timeout_s: float = 60.0, stream=None):
         _check(load().ldpc_sync(self._h, _stream(stream), float(timeout_s)))
+
+
+class CodeSet:
+    """Codes decoded together in mixed batches (the handles are kept alive)."""
+
+    def __init__(self, codes):
+        self.codes = list(codes)
+        arr = (ctypes.c_void_p * len(self.codes))(*[c._h.value for c in self.codes])
+        self._h = ctypes.c_void_p()
+        _check(load().ldpc_codeset_create(arr, len(self.codes), ctypes.byref(self._h)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.ldpc_codeset_destroy(h)
+            self._h = None
+
+    def __len__(self):
+        return len(self.codes)
+
+
+class MixedPlan:
+    """Layout and launch plan of a batch whose frame f uses code
+    code_of_frame[f] of the set."""
+
+    def __init__(self, codeset: CodeSet, code_of_frame):
+        cof = np.ascontiguousarray(code_of_frame, dtype=np.int32)
+        self.codeset = codeset
+        self.code_of_frame = cof
+        self.frames = int(cof.size)
+        self._h = ctypes.c_void_p()
+        _check(load().ldpc_mixed_plan_create(codeset._h, cof.ctypes.data_as(ctypes.c_void_p),
+                                             self.frames, ctypes.byref(self._h)))
+        v = [ctypes.c_int64() for _ in range(4)]
+        ng = ctypes.c_int()
+        _check(load().ldpc_mixed_plan_sizes(self._h, *[ctypes.byref(x) for x in v],
+                                            ctypes.byref(ng)))
+        self.llr_elems, self.info_elems, self.hard_words, self.q_words = [x.value for x in v]
+        self.n_groups = ng.value
+        self.llr_off = np.zeros(self.frames + 1, dtype=np.int64)
+        self.info_off = np.zeros(self.frames + 1, dtype=np.int64)
+        self.hard_off = np.zeros(self.frames + 1, dtype=np.int64)
+        _check(load().ldpc_mixed_plan_offsets(self._h, self.llr_off.ctypes.data_as(ctypes.c_void_p),
+                                              self.info_off.ctypes.data_as(ctypes.c_void_p),
+                                              self.hard_off.ctypes.data_as(ctypes.c_void_p)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.ldpc_mixed_plan_destroy(h)
+            self._h = None
+
+    def groups(self):
+        out = []
+        for g in range(self.n_groups):
+            v = [ctypes.c_int() for _ in range(8)]
+            _check(load().ldpc_mixed_group_info(self._h, g, *[ctypes.byref(x) for x in v]))
+            keys = ("slot_class", "codes", "smem_f32", "smem_i8", "chunk_f32", "chunk_i8",
+                    "blocks_per_sm_f32", "blocks_per_sm_i8")
+            out.append(dict(zip(keys, [x.value for x in v])))
+        return out
+
+    def _dev(self):
+        return self.codeset.codes[0].device
+
+    def empty_outputs(self):
+        torch = _torch()
+        dev = self._dev()
+        return (torch.empty((self.hard_words,), dtype=torch.int32, device=dev),
+                torch.empty((self.frames,), dtype=torch.int32, device=dev))
+
+    def quantize(self, llr, scale: float = 4.0, clip: int = 63, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((max(self.q_words, 1),), dtype=torch.int32, device=llr.device)
+        _check(load().ldpc_mixed_quantize(self._h, _ptr(llr), _ptr(out), float(scale), int(clip),
+                                          _stream(stream)))
+        return out
+
+    def decode(self, d_in, dtype: int = F32, max_iters: int = 20, alpha: float = 0.75,
+               normalise: bool = True, early_stop: bool = True, want_post: bool = False,
+               out=None, stream=None):
+        """Returns (hard int32[hard_words], iters int32[frames], post or None)."""
+        torch = _torch()
+        if out is None:
+            hard, iters = self.empty_outputs()
+            post = None
+            if want_post:
+                post = torch.empty((self.llr_elems,),
+                                   dtype=torch.float32 if dtype == F32 else torch.int8,
+                                   device=d_in.device)
+        else:
+            hard, iters, post = out
+        p = _Params(int(max_iters), float(alpha), int(bool(normalise)), int(bool(early_stop)))
+        _check(load().ldpc_decode_mixed(self._h, int(dtype), _ptr(d_in), ctypes.byref(p),
+                                        _ptr(hard), _ptr(iters), _ptr(post), _stream(stream)))
+        return hard, iters, post
+
+    def stats(self, info, hard, iters, max_iters: int, per_code: bool = True, stream=None):
+        torch = _torch()
+        cnt = torch.empty((5 + max_iters,), dtype=torch.int64, device=hard.device)
+        fe = (torch.empty((len(self.codeset),), dtype=torch.int64, device=hard.device)
+              if per_code else None)
+        _check(load().ldpc_mixed_stats(self._h, _ptr(info), _ptr(hard), _ptr(iters),
+                                       int(max_iters), _ptr(cnt), _ptr(fe), _stream(stream)))
+        return cnt, fe
+
+    def autotune(self, d_in, dtype: int = F32, max_iters: int = 20, alpha: float = 0.75,
+                 normalise: bool = True, early_stop: bool = True, reps: int = 3, out=None,
+                 stream=None):
+        hard, iters = out if out is not None else self.empty_outputs()
+        p = _Params(int(max_iters), float(alpha), int(bool(normalise)), int(bool(early_stop)))
+        _check(load().ldpc_mixed_autotune(self._h, int(dtype), _ptr(d_in), ctypes.byref(p),
+                                          _ptr(hard), _ptr(iters), int(reps), _stream(stream)))
+        return self.groups()
+
+    def scatter(self, code_index: int, what: int, src, dst, stream=None):
+        _check(load().ldpc_mixed_scatter(self._h, int(code_index), int(what), _ptr(src),
+                                         _ptr(dst), _stream(stream)))
+
+    def graph(self, dtype: int, llr, q, hard, iters, info=None, counters=None, code_fe=None,
+              max_iters: int = 20, alpha: float = 0.75, normalise: bool = True,
+              early_stop: bool = True, quant_scale: float = 4.0, quant_clip: int = 63):
+        return MixedGraph(self, dtype, llr, q, hard, iters, info, counters, code_fe,
+                          _Params(int(max_iters), float(alpha), int(bool(normalise)),
+                                  int(bool(early_stop))), quant_scale, quant_clip)
+
+
+class MixedGraph:
+    """CUDA graph of one mixed step (quantise, decode launches, stats)."""
+
+    def __init__(self, plan, dtype, llr, q, hard, iters, info, counters, code_fe, params,
+                 quant_scale, quant_clip):
+        self.plan = plan
+        self._keep = (llr, q, hard, iters, info, counters, code_fe)
+        self._h = ctypes.c_void_p()
+        _check(load().ldpc_mixed_graph_create(
+            plan._h, int(dtype), _ptr(llr), _ptr(q), float(quant_scale), int(quant_clip),
+            ctypes.byref(params), _ptr(hard), _ptr(iters), _ptr(info), _ptr(counters),
+            _ptr(code_fe), ctypes.byref(self._h)))
+
+    def launch(self, stream=None):
+        _check(load().ldpc_mixed_graph_launch(self._h, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.ldpc_mixed_graph_destroy(h)
+            self._h = None
 
 
 def gen_info(seed: int, frame0: int, frames: int, k: int, device="cuda", out=None,

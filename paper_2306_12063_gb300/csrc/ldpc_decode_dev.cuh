@@ -1,0 +1,509 @@
+// Device-side building blocks of the layered min-sum decoders (shared by
+// the single-code kernels in ldpc_decode.cu and the mixed-code kernels in
+// ldpc_mixed.cu): row processing for FP32 and packed int8, hard decisions
+// and syndrome, frame outputs, bulk-copy stage-in and work hand-out.
+#pragma once
+
+#include "ldpc_internal.cuh"
+
+namespace ldpc {
+
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kWaitLimit = 1u << 22;   // polls of a bulk-copy barrier
+
+// Row state words in shared memory (per check row):
+//   FP32: [m1, m2, meta]; m1, m2 scaled magnitudes; meta bits 0..26 hold the
+//         sign of L_mn for slot i at bit DMAX-1-i, bits 27..31 the argmin slot.
+//   int8: [M1, M2, IDX, SG0 .. SG(k-1)] (padded to an even count), one byte
+//         per frame: scaled magnitudes and argmin slot; SGk byte b bit u =
+//         sign of L_mn of frame b for slot 8k + u.
+constexpr int kRowWordsF32 = 3;
+__host__ __device__ constexpr int sign_words(int dmax) { return (dmax + 7) / 8; }
+__host__ __device__ constexpr int row_words_i8(int dmax) { return (3 + sign_words(dmax) + 1) & ~1; }
+
+__device__ __forceinline__ uint32_t lds_u32(const uint32_t *base, uint32_t byte_off) {
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(base) + byte_off);
+}
+__device__ __forceinline__ void sts_u32(uint32_t *base, uint32_t byte_off, uint32_t v) {
+    *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(base) + byte_off) = v;
+}
+
+// Fixed-width bit helpers (single instructions).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
+}
+// min(max(a + b, lo), hi) on two 16-bit lanes holding non-negative values
+// (a + b < 65536 per lane); the add and the max issue as one instruction.
+__device__ __forceinline__ uint32_t add_clamp_u16x2(uint32_t a, uint32_t b, uint32_t lo,
+                                                    uint32_t hi) {
+    const uint32_t r = __viaddmax_u16x2(a, b, lo);
+    uint32_t o;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(hi));
+    return o;
+}
+// Bytes 0, 2 (resp. 1, 3) of x zero-extended into two 16-bit lanes.
+__device__ __forceinline__ uint32_t lanes_even(uint32_t x) { return prmt(x, 0u, 0x4240u); }
+__device__ __forceinline__ uint32_t lanes_odd(uint32_t x) { return prmt(x, 0u, 0x4341u); }
+// Low bytes of the lanes of e (frames 0, 2) and o (frames 1, 3) back into one word.
+__device__ __forceinline__ uint32_t lanes_join(uint32_t e, uint32_t o) { return prmt(e, o, 0x6240u); }
+// Per byte: 0xFF where a < b, for a, b <= 127.
+__device__ __forceinline__ uint32_t lt_mask7(uint32_t a, uint32_t b) {
+    return msb_bytes_to_mask(b + 0x7F7F7F7Fu - a);
+}
+// Per byte: 0xFF where x != 0, for x <= 128.
+__device__ __forceinline__ uint32_t nonzero_mask(uint32_t x) {
+    return msb_bytes_to_mask(x + 0x7F7F7F7Fu);
+}
+// Per byte floor(3 m / 4) = m - ceil(m / 4), m <= 127 (no carry crosses bytes).
+__device__ __forceinline__ uint32_t scale34(uint32_t m) {
+    return m - (((m + 0x03030303u) >> 2) & 0x3F3F3F3Fu);
+}
+
+
+// ---------------------------------------------------------------------------
+// Row processing.  Every row runs all DMAX edge slots as straight-line code
+// (so the compiler can interleave the slots freely); a layer of degree d uses
+// slots DMAX-d .. DMAX-1 and the leading slots read a dummy posterior (word N
+// of the posterior array) whose value leaves the row's minimum, second
+// minimum, sign parity and syndrome unchanged.  Stores are made only for the
+// real slots.
+// ---------------------------------------------------------------------------
+
+// FP32 layer: eq. (22) Z_mn = Z_n - L_mn; eq. (23) new L_mn from the
+// smallest and second smallest |Z_mn| and the product of signs; eq. (20) in
+// single-scan form Z_n = Z_mn + L_mn.  Each float operation is an explicitly
+// rounded intrinsic, so no multiply-add is ever contracted.  The dummy
+// posterior is +inf: |Z_mn| = +inf is never a minimum and its sign is +.
+//
+// WT (learned normalised min-sum): the message of edge q in iteration k is
+// w[k-1][q] times the unscaled magnitude, q numbering the nonzero blocks of
+// H_bm row by row.  The row state then keeps the unscaled minima and the
+// message signs before weighting.  wprev / wcur point at this layer's
+// weights of the previous and the current iteration, staged in shared memory
+// in slot order (wpad(DMAX) floats per layer, 16-byte aligned, zero in the
+// leading unused slots).  Since rounding is symmetric in sign,
+// (w |m|) with the sign of m applied afterwards equals w m: one multiply per
+// slot on the signed message.
+__host__ __device__ constexpr int wpad(int dmax) { return (dmax + 3) & ~3; }
+
+template <int DMAX, bool WT = false>
+__device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t *Zs,
+                                          uint32_t *rows, int lane, bool norm, float alpha,
+                                          const float *wprev = nullptr,
+                                          const float *wcur = nullptr) {
+    const uint32_t ri = __ldg(c.rowinfo + layer);
+    const int d = ri & 255;
+    const int start = DMAX - d;
+    float wp[WT ? wpad(DMAX) : 1], wc[WT ? wpad(DMAX) : 1];
+    if (WT) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(wprev);
+        const float4 *c4 = reinterpret_cast<const float4 *>(wcur);
+#pragma unroll
+        for (int j = 0; j < wpad(DMAX) / 4; ++j) {
+            const float4 a = p4[j], b = c4[j];
+            wp[WT ? 4 * j : 0] = a.x; wp[WT ? 4 * j + 1 : 0] = a.y;
+            wp[WT ? 4 * j + 2 : 0] = a.z; wp[WT ? 4 * j + 3 : 0] = a.w;
+            wc[WT ? 4 * j : 0] = b.x; wc[WT ? 4 * j + 1 : 0] = b.y;
+            wc[WT ? 4 * j + 2 : 0] = b.z; wc[WT ? 4 * j + 3 : 0] = b.w;
+        }
+    }
+    for (int t = 0; t < c.rpl; ++t) {
+        const int r = lane + 32 * t;
+        if (r >= c.z) break;
+        uint32_t *rs = rows + (layer * c.z + r) * kRowWordsF32;
+        const float m1 = __uint_as_float(rs[0]), m2 = __uint_as_float(rs[1]);
+        const uint32_t meta = rs[2];
+        const int idx = static_cast<int>(meta >> 27);
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
+        uint32_t off[DMAX];
+        float Q[DMAX];
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) Q[i] = __uint_as_float(lds_u32(Zs, off[i]));
+        float mn1 = __int_as_float(0x7F800000), mn2 = mn1;
+        uint32_t sx = 0;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const float mag = (idx == i) ? m2 : m1;
+            // slot i's sign bit moved to bit 31 (a multiply, so it may issue
+            // on the FMA pipe)
+            const uint32_t sbit = (meta * (1u << (i + 32 - DMAX))) & 0x80000000u;
+            const float Lu = __uint_as_float(__float_as_uint(mag) | sbit);
+            const float L = WT ? __fmul_rn(wp[WT ? i : 0], Lu) : Lu;
+            const float q = __fsub_rn(Q[i], L);
+            Q[i] = q;
+            const float a = fabsf(q);
+            mn2 = fmaxf(mn1, fminf(mn2, a));
+            mn1 = fminf(mn1, a);
+            sx ^= __float_as_uint(q);
+        }
+        const float n1 = (norm && !WT) ? __fmul_rn(alpha, mn1) : mn1;
+        const float n2 = (norm && !WT) ? __fmul_rn(alpha, mn2) : mn2;
+        const uint32_t S = sx & 0x80000000u;
+        const uint32_t s1 = __float_as_uint(n1) | S, s2 = __float_as_uint(n2) | S;
+        uint32_t nsg = 0;
+        int id = 0;
+        // an edge whose |Z_mn| equals the minimum gets the second minimum (on
+        // ties both minima are equal, so any such edge may be the argmin)
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const bool at_min = fabsf(Q[i]) == mn1;
+            const uint32_t ms = at_min ? s2 : s1;
+            id = at_min ? i : id;
+            const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);
+            // learned weights: w times the signed message
+            const uint32_t Lw = WT ? __float_as_uint(__fmul_rn(wc[WT ? i : 0], __uint_as_float(L)))
+                                   : L;
+            if (i >= start)
+                sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(Lw))));
+            nsg = __funnelshift_l(L, nsg, 1);
+        }
+        rs[0] = __float_as_uint(n1);
+        rs[1] = __float_as_uint(n2);
+        rs[2] = nsg | (static_cast<uint32_t>(id) << 27);
+    }
+}
+
+// FP32 hard decision (eq. 21) and syndrome: true when every check holds.
+template <int DMAX>
+__device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t *Zs, int lane) {
+    uint32_t bad = 0;
+    for (int l = 0; l < c.mb; ++l) {
+        for (int t = 0; t < c.rpl; ++t) {
+            if (lane + 32 * t >= c.z) break;
+            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
+            uint32_t off[DMAX];
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+            uint32_t par = 0;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) {
+                const uint32_t u = lds_u32(Zs, off[i]);
+                par ^= (u - 1u) | u;   // bit 31 set iff Z <= 0 (negatives, -0 and +0)
+            }
+            bad |= par;
+        }
+    }
+    return !__any_sync(kFull, bad >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// int8 layer, four frames per word.  Posteriors live in shared memory in
+// offset form (Z + 128, one byte per frame, values 1..255) and so does Z_mn
+// inside the row.  The check side works byte-wise: |Z_mn| = |x - 128| (one
+// absolute-difference instruction), the running minimum, second minimum and
+// argmin with compare masks from prmt's sign replication, and the sign
+// parity.  The saturating additions Z_mn = Z_n - L_mn and Z_n = Z_mn + L_mn
+// run on two 16-bit lanes per word (frames 0, 2 and 1, 3) holding
+// non-negative biased values, clamped with packed u16 add-max and min.  The
+// dummy posterior is +127 and the leading slots' stored message sign is
+// kept negative, so their Z_mn clamps to +127: never below a minimum.
+// ---------------------------------------------------------------------------
+template <int DMAX>
+__device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *Zs, uint32_t *rows,
+                                         int lane, bool norm) {
+    constexpr int SGW = sign_words(DMAX);
+    const uint32_t ri = __ldg(c.rowinfo + layer);
+    const int d = ri & 255;
+    const int start = DMAX - d;
+    // sign bits forced on for the leading (unused) slots, per sign word
+    uint32_t pad[SGW];
+#pragma unroll
+    for (int k = 0; k < SGW; ++k) {
+        const int nb = min(max(start - 8 * k, 0), 8);
+        pad[k] = ((1u << nb) - 1u) * 0x01010101u;
+    }
+    for (int t = 0; t < c.rpl; ++t) {
+        const int r = lane + 32 * t;
+        if (r >= c.z) break;
+        uint32_t *rs = rows + (layer * c.z + r) * row_words_i8(DMAX);
+        const uint32_t M1 = rs[0], M2 = rs[1], IDX = rs[2];
+        uint32_t SG[SGW];
+#pragma unroll
+        for (int k = 0; k < SGW; ++k) SG[k] = rs[3 + k];
+        // offset-128 bytes of -L_old for the four (sign, magnitude) cases
+        const uint32_t P1c = 0x80808080u - M1, P2c = 0x80808080u - M2;   // L > 0
+        const uint32_t N1c = 0x80808080u | M1, N2c = 0x80808080u | M2;   // L < 0
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
+        uint32_t off[DMAX], Q[DMAX];
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) Q[i] = lds_u32(Zs, off[i]);
+        uint32_t A[DMAX];
+        uint32_t mn1 = 0x7F7F7F7Fu, mn2 = 0x7F7F7F7Fu, sx = 0;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t u = Q[i];
+            const uint32_t sm = msb_bytes_to_mask(SG[i >> 3] << (7 - (i & 7)));
+            const uint32_t nq = nonzero_mask(IDX ^ (0x01010101u * i));
+            const uint32_t nl = bsel(bsel(P2c, P1c, nq), bsel(N2c, N1c, nq), sm);
+            // (Z + 128) + (128 - L) = Z_mn + 256, clamped to Z_mn in [-127, 127]
+            const uint32_t qe =
+                add_clamp_u16x2(lanes_even(u), lanes_even(nl), 0x00810081u, 0x017F017Fu);
+            const uint32_t qo =
+                add_clamp_u16x2(lanes_odd(u), lanes_odd(nl), 0x00810081u, 0x017F017Fu);
+            const uint32_t x = lanes_join(qe, qo) ^ 0x80808080u;   // offset form of Z_mn
+            Q[i] = x;
+            const uint32_t a = __vabsdiffu4(x, 0x80808080u);       // |Z_mn|
+            A[i] = a;
+            const uint32_t lt = lt_mask7(a, mn1);
+            const uint32_t tmax = bsel(a, mn1, lt);
+            mn1 = bsel(mn1, a, lt);
+            mn2 = bsel(mn2, tmax, lt_mask7(tmax, mn2));
+            sx ^= x;
+        }
+        const uint32_t n1 = norm ? scale34(mn1) : mn1;
+        const uint32_t n2 = norm ? scale34(mn2) : mn2;
+        // offset bytes have bit 7 set for Z_mn >= 0: flip once per slot
+        const uint32_t S = (sx ^ ((DMAX & 1) ? 0x80808080u : 0u)) & 0x80808080u;
+        // offset-128 bytes of L_new for the four (sign, magnitude) cases
+        const uint32_t Lp1 = 0x80808080u | n1, Lp2 = 0x80808080u | n2;       // L > 0
+        const uint32_t Ln1 = 0x80808080u - n1, Ln2 = 0x80808080u - n2;       // L < 0
+        uint32_t nsg[SGW];
+#pragma unroll
+        for (int k = 0; k < SGW; ++k) nsg[k] = pad[k];
+        uint32_t id = 0;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t x = Q[i];
+            const uint32_t nm = msb_bytes_to_mask(~(x ^ S));   // 0xFF: L_new < 0 (S xor Z_mn < 0)
+            // |Z_mn| >= min, so min + 128 - |Z_mn| lies in [1, 128] and equals
+            // 128 exactly at the minimum: that edge gets the second minimum (on
+            // ties both minima are equal, so any such edge may be the argmin)
+            const uint32_t at_min = msb_bytes_to_mask(mn1 + 0x80808080u - A[i]);
+            id = bsel(id, 0x01010101u * i, at_min);
+            const uint32_t y = bsel(bsel(Lp1, Lp2, at_min), bsel(Ln1, Ln2, at_min), nm);
+            // (Z_mn + 128) + (L + 128) = Z + 256, clamped to Z in [-127, 127]
+            const uint32_t ze =
+                add_clamp_u16x2(lanes_even(x), lanes_even(y), 0x00810081u, 0x017F017Fu);
+            const uint32_t zo =
+                add_clamp_u16x2(lanes_odd(x), lanes_odd(y), 0x00810081u, 0x017F017Fu);
+            if (i >= start) sts_u32(Zs, off[i], lanes_join(ze, zo) ^ 0x80808080u);
+            nsg[i >> 3] |= nm & ((1u << (i & 7)) * 0x01010101u);
+        }
+        rs[0] = n1;
+        rs[1] = n2;
+        rs[2] = id;
+#pragma unroll
+        for (int k = 0; k < SGW; ++k) rs[3 + k] = nsg[k];
+    }
+}
+
+// int8 hard decision per byte: bit 7 set where Z <= 0, i.e. offset value <= 128.
+__device__ __forceinline__ uint32_t hard_bytes_off(uint32_t u) {
+    return ~(u - 0x01010101u) & 0x80808080u;   // u >= 1: no borrow crosses bytes
+}
+
+// int8 syndrome: bit 7 of byte b set when frame b has an unsatisfied check.
+template <int DMAX>
+__device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint32_t *Zs,
+                                                    int lane) {
+    uint32_t bad = 0;
+    for (int l = 0; l < c.mb; ++l) {
+        for (int t = 0; t < c.rpl; ++t) {
+            if (lane + 32 * t >= c.z) break;
+            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
+            uint32_t off[DMAX];
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+            // bit 7 of (u - 1) is set iff Z >= 1, so each of the DMAX terms (the
+            // dummy +127 ones included) flips the parity of the hard decisions
+            uint32_t par = (DMAX & 1) ? 0x80808080u : 0u;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i)
+                par ^= lds_u32(Zs, off[i]) - 0x01010101u;   // bytes >= 1: no borrow
+            bad |= par;
+        }
+    }
+    return __reduce_or_sync(kFull, bad & 0x80808080u);
+}
+
+// ---------------------------------------------------------------------------
+// Outputs of one frame: packed hard decisions, iteration count, posteriors.
+// ---------------------------------------------------------------------------
+// h: the frame's ceil(N/32) hard-decision words; it_out: its iteration
+// count; p: its N posteriors or NULL.
+__device__ __forceinline__ void write_frame_f32_to(const DevCode &c, const uint32_t *Zs, int it,
+                                                   uint32_t *h, int32_t *it_out, float *p,
+                                                   int lane) {
+    for (int wb = 0; wb < c.nwords; wb += 32) {
+        uint32_t mine = 0;
+        for (int i = 0; i < 32 && wb + i < c.nwords; ++i) {
+            const int n = (wb + i) * 32 + lane;
+            const bool b = n < c.n && !(__uint_as_float(Zs[n]) > 0.0f);
+            const uint32_t bal = __ballot_sync(kFull, b);
+            if (lane == i) mine = bal;
+        }
+        if (wb + lane < c.nwords) h[wb + lane] = mine;
+    }
+    if (lane == 0) *it_out = it;
+    if (p)
+        for (int n = lane; n < c.n; n += 32) p[n] = __uint_as_float(Zs[n]);
+}
+
+__device__ __forceinline__ void write_frame_f32(const DevCode &c, const uint32_t *Zs, int64_t f,
+                                                int it, uint32_t *hard, int32_t *iters,
+                                                float *post, int lane) {
+    write_frame_f32_to(c, Zs, it, hard + f * c.nwords, iters + f, post ? post + f * c.n : nullptr,
+                       lane);
+}
+
+// Outputs of byte lane `byte` (one frame of the packed word).
+__device__ __forceinline__ void write_frame_i8_to(const DevCode &c, const uint32_t *Zs, int byte,
+                                                  int it, uint32_t *h, int32_t *it_out,
+                                                  int8_t *p, int lane) {
+    const int sh = 8 * byte + 7;
+    for (int wb = 0; wb < c.nwords; wb += 32) {
+        uint32_t mine = 0;
+        for (int i = 0; i < 32 && wb + i < c.nwords; ++i) {
+            const int n = (wb + i) * 32 + lane;
+            const bool b = n < c.n && ((hard_bytes_off(Zs[n]) >> sh) & 1u);
+            const uint32_t bal = __ballot_sync(kFull, b);
+            if (lane == i) mine = bal;
+        }
+        if (wb + lane < c.nwords) h[wb + lane] = mine;
+    }
+    if (lane == 0) *it_out = it;
+    if (p)
+        for (int n = lane; n < c.n; n += 32)
+            p[n] = static_cast<int8_t>(((Zs[n] >> (8 * byte)) & 0xFFu) ^ 0x80u);
+}
+
+__device__ __forceinline__ void write_frame_i8(const DevCode &c, const uint32_t *Zs, int64_t f,
+                                               int byte, int it, uint32_t *hard, int32_t *iters,
+                                               int8_t *post, int lane) {
+    write_frame_i8_to(c, Zs, byte, it, hard + f * c.nwords, iters + f,
+                      post ? post + f * c.n : nullptr, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Stage-in helpers.
+// ---------------------------------------------------------------------------
+// Bulk copy of n words from global to Zs, bounded wait.  Returns false (whole
+// warp) if the copy did not complete in time; the status word records it.
+__device__ __forceinline__ bool stage_bulk(const DevCode &c, uint32_t *Zs, const uint32_t *src,
+                                           uint64_t *bar, uint32_t &phase, int lane) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(c.n) * 4u);
+        bulk_copy_g2s(Zs, src, static_cast<uint32_t>(c.n) * 4u, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase, kWaitLimit);
+    if (!__all_sync(kFull, ok)) {
+        if (lane == 0) atomicOr(c.status, kStatusCopyTimeout);
+        mbar_wait_bounded(bar, phase, kWaitLimit);   // let the copy land before leaving
+        return false;
+    }
+    phase ^= 1u;
+    return true;
+}
+
+__device__ __forceinline__ int64_t next_work(unsigned long long *ctr, int64_t base, int lane) {
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(ctr, 1ull);
+    v = __shfl_sync(kFull, v, 0);
+    return base + static_cast<int64_t>(v);
+}
+
+// ---------------------------------------------------------------------------
+// One FP32 frame: stage its LLRs (src, N words) into Zs, clear the messages,
+// run the layered iterations (eq. 22, 23, 20) with the syndrome stop after
+// each full iteration (eq. 21, Section 4 step 4).  Returns the iteration
+// count, or 0 if the bulk copy timed out (the status word records it).
+// Learned weights (WT) are staged per iteration into wbuf.
+// ---------------------------------------------------------------------------
+template <int DMAX, bool WT>
+__device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, uint32_t *rows,
+                                              float *wbuf, const uint32_t *src, bool use_bulk,
+                                              uint64_t *bar, uint32_t &phase,
+                                              const DecodeParams &p, int lane) {
+    if (use_bulk) {
+        if (!stage_bulk(c, Zs, src, bar, phase, lane)) return 0;
+    } else {
+        for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i);
+    }
+    for (int i = lane; i < c.m * kRowWordsF32; i += 32) rows[i] = 0u;   // all L_mn = 0
+    __syncwarp();
+    const bool norm = p.normalise != 0;
+    for (int k = 1; k <= p.max_iters; ++k) {
+        constexpr int WP = wpad(DMAX);
+        float *wcur = wbuf + (k & 1) * c.mb * WP;
+        const float *wprev = k > 1 ? wbuf + ((k - 1) & 1) * c.mb * WP : wcur;
+        if (WT) {
+            // stage w[k-1] in slot order; iteration 1 also serves as its own
+            // "previous" weights (they multiply zero messages)
+            const float *wk = p.weights + static_cast<size_t>(k - 1) * p.n_edges;
+            for (int i = lane; i < c.mb * WP; i += 32) {
+                const int g = __ldg(c.wgather + i);
+                wcur[i] = g >= 0 ? __ldg(wk + g) : 0.0f;
+            }
+            __syncwarp();
+        }
+        for (int l = 0; l < c.mb; ++l) {
+            layer_f32<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
+                                wcur + l * WP);
+            __syncwarp();
+        }
+        if (p.early_stop && syndrome_ok_f32<DMAX>(c, Zs, lane)) return k;
+    }
+    return p.max_iters;
+}
+
+// ---------------------------------------------------------------------------
+// Evaluation of one decoded frame (Section 6.1 error counting): the number of
+// info bits (the first K hard decisions) that differ from the sent ones, and
+// whether the hard decisions satisfy every check (eq. 21 termination test),
+// both warp-uniform.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long frame_outcome(const DevCode &c, const uint8_t *in,
+                                                            const uint32_t *h, int lane,
+                                                            bool *syn_ok) {
+    unsigned long long errs = 0;
+    for (int t = lane; t < c.k; t += 32) errs += ((h[t >> 5] >> (t & 31)) & 1u) ^ (in[t] & 1u);
+    uint32_t bad = 0;
+    for (int l = 0; l < c.mb; ++l) {
+        const int d = c.rowinfo[l] & 255;
+        for (int t = 0; t < c.rpl; ++t) {
+            if (lane + 32 * t >= c.z) continue;
+            uint32_t par = 0;
+            for (int e = 0; e < d; ++e) {
+                const int slot = c.dslots - d + e;
+                const int v = c.voff[((l * c.rpl + t) * c.dslots + slot) * 32 + lane] >> 2;
+                par ^= (h[v >> 5] >> (v & 31)) & 1u;
+            }
+            bad |= par;
+        }
+    }
+    for (int o = 16; o; o >>= 1) errs += __shfl_xor_sync(kFull, errs, o);
+    *syn_ok = !__any_sync(kFull, bad);
+    return errs;
+}
+
+// Counter layout of ldpc_frame_stats: [0] bit errors, [1] frame errors,
+// [2] undetected frame errors, [3] iteration sum, [4 + t] frames ending at t.
+__device__ __forceinline__ void count_frame(unsigned long long *cnt, unsigned long long errs,
+                                            bool syn_ok, int it, int max_iters) {
+    if (errs) {
+        atomicAdd(&cnt[0], errs);
+        atomicAdd(&cnt[1], 1ull);
+        if (syn_ok) atomicAdd(&cnt[2], 1ull);
+    }
+    atomicAdd(&cnt[3], static_cast<unsigned long long>(it));
+    if (it >= 0 && it <= max_iters) atomicAdd(&cnt[4 + it], 1ull);
+}
+
+// Fixed-point channel value of one LLR (Section 5, 8 bits):
+// rint(clamp(scale * llr, -clip, clip)), round half to even.
+__device__ __forceinline__ uint32_t quantize_one(float llr, float scale, float fc) {
+    float x = __fmul_rn(scale, llr);
+    x = fminf(fmaxf(x, -fc), fc);
+    return static_cast<uint32_t>(__float2int_rn(x)) & 0xFFu;
+}
+
+}  // namespace ldpc

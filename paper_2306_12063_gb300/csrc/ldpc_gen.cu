@@ -4,7 +4,7 @@
 // and error counting (the evaluation of Section 6.1).
 #include <algorithm>
 
-#include "ldpc_internal.cuh"
+#include "ldpc_decode_dev.cuh"
 
 namespace ldpc {
 
@@ -270,13 +270,9 @@ __global__ void quantize_kernel(const float *__restrict__ llr, uint32_t *__restr
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int64_t f = 4 * g + b;
-            int v = clip;
-            if (f < frames) {
-                float x = __fmul_rn(scale, llr[f * n + p]);
-                x = fminf(fmaxf(x, -fc), fc);
-                v = __float2int_rn(x);
-            }
-            word |= (static_cast<uint32_t>(v) & 0xFFu) << (8 * b);
+            const uint32_t v = f < frames ? quantize_one(llr[f * n + p], scale, fc)
+                                          : static_cast<uint32_t>(clip);
+            word |= v << (8 * b);
         }
         q[t] = word;
     }
@@ -291,38 +287,10 @@ __global__ void stats_kernel(DevCode c, const uint8_t *__restrict__ info,
     const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     for (int64_t f = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
          f < frames; f += warps) {
-        const uint32_t *h = hard + f * c.nwords;
-        const uint8_t *in = info + f * c.k;
-        unsigned long long errs = 0;
-        for (int t = lane; t < c.k; t += 32) errs += ((h[t >> 5] >> (t & 31)) & 1u) ^ (in[t] & 1u);
-        // syndrome of the hard decisions (eq. 21 termination test)
-        uint32_t bad = 0;
-        for (int l = 0; l < c.mb; ++l) {
-            const uint32_t ri = c.rowinfo[l];
-            const int d = ri & 255;
-            for (int t = 0; t < c.rpl; ++t) {
-                if (lane + 32 * t >= c.z) continue;
-                uint32_t par = 0;
-                for (int e = 0; e < d; ++e) {
-                    const int slot = c.dslots - d + e;
-                    const int v = c.voff[((l * c.rpl + t) * c.dslots + slot) * 32 + lane] >> 2;
-                    par ^= (h[v >> 5] >> (v & 31)) & 1u;
-                }
-                bad |= par;
-            }
-        }
-        for (int o = 16; o; o >>= 1) errs += __shfl_xor_sync(0xFFFFFFFFu, errs, o);
-        const bool syn_ok = !__any_sync(0xFFFFFFFFu, bad);
-        if (lane == 0) {
-            const int it = iters[f];
-            if (errs) {
-                atomicAdd(&cnt[0], errs);
-                atomicAdd(&cnt[1], 1ull);
-                if (syn_ok) atomicAdd(&cnt[2], 1ull);
-            }
-            atomicAdd(&cnt[3], static_cast<unsigned long long>(it));
-            if (it >= 0 && it <= max_iters) atomicAdd(&cnt[4 + it], 1ull);
-        }
+        bool syn_ok;
+        const unsigned long long errs =
+            frame_outcome(c, info + f * c.k, hard + f * c.nwords, lane, &syn_ok);
+        if (lane == 0) count_frame(cnt, errs, syn_ok, iters[f], max_iters);
     }
 }
 

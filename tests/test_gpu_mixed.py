@@ -1,0 +1,142 @@
+"""Mixed-code batches (one persistent launch per launch group) against the
+oracle, frame by frame: every frame decoded by the mixed FP32 and int8
+kernels must equal the oracle's decode of that frame with its own code
+(hard decisions, iteration counts, posteriors), whatever the interleaving
+of codes, the work-item sizes the autotuner picks, or the graph replay."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ldpc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2306_12063_gb300 import _build
+    _build.build()
+    import paper_2306_12063_gb300 as m
+    m.load()
+    return m
+
+
+def _shapes():
+    full = synth.wimax_mixed_set()
+    # rates 1/2 .. 5/6 at small, middle and the largest Z, plus the two Wi-Fi codes
+    pick = [full[i] for i in (0, 1, 2, 3, 36, 37, 38, 39, 72, 73, 74, 75)]
+    return pick + [synth.wifi_n648_r12(), synth.wifi_n1944_r56()]
+
+
+def _setup(ldpc, shapes, frames, seed, ebn0=(1.5, 4.5)):
+    from paper_2306_12063_gb300.workload import make_mixed_batch
+    codes = [ldpc.Code(s.hbm, s.z) for s in shapes]
+    cs = ldpc.CodeSet(codes)
+    rng = np.random.default_rng(seed)
+    cof = rng.integers(0, len(shapes), frames).astype(np.int32)
+    plan = ldpc.MixedPlan(cs, cof)
+    batch = make_mixed_batch(plan, ebn0)
+    return codes, cs, plan, batch
+
+
+def _oracle_per_code(shapes, plan, llr_host, dtype, max_iters):
+    """Oracle decode of every frame with its own code; returns per-frame
+    (hard words, iters, post)."""
+    out = {}
+    for ci, s in enumerate(shapes):
+        idx = np.nonzero(plan.code_of_frame == ci)[0]
+        if idx.size == 0:
+            continue
+        rc = oracle.RefCode(s.hbm, s.z)
+        x = np.stack([llr_host[plan.llr_off[f]:plan.llr_off[f] + rc.n] for f in idx])
+        if dtype == "f32":
+            h, it, p = rc.decode_layered_f32(x, max_iters, 0.75, True, True)
+        else:
+            h, it, p, _ = rc.decode_layered_i8(oracle.quantize_i8(x), max_iters, True, True)
+        for j, f in enumerate(idx):
+            out[int(f)] = (h[j], it[j], p[j])
+    return out
+
+
+def _check_frames(plan, ref, hard, iters, post):
+    hard = hard.cpu().numpy().view(np.uint32)
+    iters = iters.cpu().numpy()
+    post = post.cpu().numpy()
+    for f in range(plan.frames):
+        h, it, p = ref[f]
+        a, b = plan.hard_off[f], plan.hard_off[f + 1]
+        assert iters[f] == it, f
+        assert (hard[a:b] == h).all(), f
+        assert (post[plan.llr_off[f]:plan.llr_off[f + 1]] == p).all(), f
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_mixed_bit_exact_against_oracle(ldpc, dtype):
+    shapes = _shapes()
+    codes, cs, plan, batch = _setup(ldpc, shapes, 700, seed=4)
+    assert plan.n_groups >= 4
+    if dtype == "f32":
+        d_in, dt = batch.llr, ldpc.F32
+    else:
+        d_in, dt = plan.quantize(batch.llr), ldpc.I8X4
+    hard, iters, post = plan.decode(d_in, dt, max_iters=20, want_post=True)
+    ref = _oracle_per_code(shapes, plan, batch.llr.cpu().numpy(), dtype, 20)
+    _check_frames(plan, ref, hard, iters, post)
+    # after autotuning (other work-item sizes and residency caps) still exact
+    plan.autotune(d_in, dt, max_iters=20, reps=1)
+    hard2, iters2, post2 = plan.decode(d_in, dt, max_iters=20, want_post=True)
+    assert torch.equal(hard, hard2) and torch.equal(iters, iters2) and torch.equal(post, post2)
+
+
+def test_mixed_unaligned_codes_and_single_code(ldpc):
+    """Codes with N not a multiple of 4 (plain-load path) and a batch with one
+    code only."""
+    shapes = [synth.random_small_code(9, 5, 13, 3), synth.random_small_code(2, 4, 11, 7),
+              synth.tiny_z3_code()]
+    assert any(s.hbm.shape[1] * s.z % 4 for s in shapes)
+    codes, cs, plan, batch = _setup(ldpc, shapes, 157, seed=8, ebn0=(0.5, 3.0))
+    for dtype in ("f32", "i8"):
+        d_in = batch.llr if dtype == "f32" else plan.quantize(batch.llr)
+        dt = ldpc.F32 if dtype == "f32" else ldpc.I8X4
+        hard, iters, post = plan.decode(d_in, dt, max_iters=12, want_post=True)
+        ref = _oracle_per_code(shapes, plan, batch.llr.cpu().numpy(), dtype, 12)
+        _check_frames(plan, ref, hard, iters, post)
+    one = [synth.wimax_mixed_set()[40]]
+    codes, cs, plan, batch = _setup(ldpc, one, 33, seed=2)
+    hard, iters, post = plan.decode(batch.llr, ldpc.F32, max_iters=20, want_post=True)
+    ref = _oracle_per_code(one, plan, batch.llr.cpu().numpy(), "f32", 20)
+    _check_frames(plan, ref, hard, iters, post)
+
+
+def test_mixed_stats_and_graph(ldpc):
+    shapes = _shapes()
+    codes, cs, plan, batch = _setup(ldpc, shapes, 900, seed=6, ebn0=(1.0, 3.0))
+    q = plan.quantize(batch.llr)
+    hard, iters, _ = plan.decode(q, ldpc.I8X4, max_iters=20)
+    cnt, fe = plan.stats(batch.info, hard, iters, 20)
+    # per-code frame errors from the unpacked hard decisions
+    hw = hard.cpu().numpy().view(np.uint32)
+    info = batch.info.cpu().numpy()
+    want = np.zeros(len(shapes), dtype=np.int64)
+    for f in range(plan.frames):
+        c = codes[plan.code_of_frame[f]]
+        bits = oracle.unpack_hard(hw[plan.hard_off[f]:plan.hard_off[f + 1]][None], c.n)[0]
+        want[plan.code_of_frame[f]] += int((bits[:c.k] != info[plan.info_off[f]:
+                                                               plan.info_off[f + 1]]).any())
+    assert (fe.cpu().numpy() == want).all()
+    assert cnt[1].item() == want.sum() > 0
+    assert cnt[3].item() == int(iters.sum().item())
+    # the captured step (quantise, decode groups, stats) replays the same results
+    h2, i2 = plan.empty_outputs()
+    q2 = torch.empty_like(q)
+    c2 = torch.empty_like(cnt)
+    f2 = torch.empty_like(fe)
+    g = plan.graph(ldpc.I8X4, batch.llr, q2, h2, i2, batch.info, c2, f2, max_iters=20)
+    for _ in range(2):
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(h2, hard) and torch.equal(i2, iters)
+        assert torch.equal(c2, cnt) and torch.equal(f2, fe) and torch.equal(q2, q)
