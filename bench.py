@@ -268,6 +268,115 @@ def learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
                          "kernels": "ldpc_learned_train_forward/backward, ldpc_adam_step"}}
 
 
+MIXED_WORKLOAD = ("WiMAX-shaped mixed set: 76 codes, N = 24 Z for Z = 24..96 step 4, rates "
+                  "1/2, 2/3, 3/4, 5/6 (seed 3); frames interleaved at random over the codes "
+                  "(seed 3), Eb/N0 uniform in [1.5, 4.5) dB per frame, max 20 iterations, "
+                  "early stop")
+
+
+def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
+    """Mixed-size batch: one persistent launch per launch group (autotuned,
+    captured in a CUDA graph with the quantiser and the error counting),
+    against the same frames decoded by one single-code launch per code."""
+    from paper_2306_12063_gb300.shard import reduce_counters
+    from paper_2306_12063_gb300.workload import make_mixed_batch, mixed_frame_id
+
+    shapes = synth.wimax_mixed_set()
+    codes = [ldpc.Code(s.hbm, s.z, device=dev) for s in shapes]
+    cs = ldpc.CodeSet(codes)
+    F = args.mixed_frames
+    cof, _ = synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)
+    cof = np.ascontiguousarray(cof[rank * F:(rank + 1) * F])
+    plan = ldpc.MixedPlan(cs, cof)
+    batch = make_mixed_batch(plan, LEARNED_EBN0, seed=1)
+    q = plan.quantize(batch.llr)
+    hard, iters = plan.empty_outputs()
+    info_bits = int(plan.info_elems)
+    edges_iter = np.array([int((s.hbm >= 0).sum()) * s.z for s in shapes], dtype=np.int64)
+    res = {"workload": MIXED_WORKLOAD, "frames": F * ws, "codes": len(shapes),
+           "launch_groups": plan.n_groups}
+    steps = max(1, args.steps // 2)
+
+    def time_fn(fn):
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = a.elapsed_time(b) / steps
+        if pg is not None:
+            tt = torch.tensor([ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    # per-code reference layout: each code's frames contiguous (single-code kernels)
+    counts = np.bincount(cof, minlength=len(shapes))
+    per_code = []
+    for ci, code in enumerate(codes):
+        if counts[ci] == 0:
+            continue
+        f0 = mixed_frame_id(ci, 0)
+        inf_c = ldpc.gen_info(1, f0, int(counts[ci]), code.k, device=dev)
+        cw = code.encode(inf_c)
+        sig = ldpc.snr_sigma(1, f0, int(counts[ci]), LEARNED_EBN0[0], LEARNED_EBN0[1],
+                             code.k / code.n, device=dev)
+        llr_c = ldpc.awgn_llr_frames(cw, f0, 1, sig)
+        per_code.append((code, llr_c, ldpc.quantize_pack_i8(llr_c), int(counts[ci])))
+    del cw
+
+    for name, dt, d_in in (("int8", ldpc.I8X4, q), ("fp32", ldpc.F32, batch.llr)):
+        t0 = time.time()
+        plan.autotune(d_in, dt, max_iters=MAX_ITERS, reps=3, out=(hard, iters))
+        groups = plan.autotune(d_in, dt, max_iters=MAX_ITERS, reps=3, out=(hard, iters))
+        tune_s = time.time() - t0
+        direct_ms = time_fn(lambda: plan.decode(d_in, dt, max_iters=MAX_ITERS,
+                                                out=(hard, iters, None)))
+        cnt = torch.empty((5 + MAX_ITERS,), dtype=torch.int64, device=dev)
+        fe = torch.empty((len(shapes),), dtype=torch.int64, device=dev)
+        qg = torch.empty_like(q)
+        g = plan.graph(dt, batch.llr, qg if dt == ldpc.I8X4 else None, hard, iters, batch.info,
+                       cnt, fe, max_iters=MAX_ITERS)
+        graph_ms = time_fn(lambda: g.launch())
+        st = reduce_counters(cnt.cpu().numpy())
+
+        def per_code_step():
+            for code, llr_c, q_c, n_c in per_code:
+                if dt == ldpc.I8X4:
+                    code.decode(q_c, frames=n_c, dtype=dt, max_iters=MAX_ITERS, early_stop=True)
+                else:
+                    code.decode(llr_c, dtype=dt, max_iters=MAX_ITERS, early_stop=True)
+
+        pc_ms = time_fn(per_code_step)
+        nf = F * ws
+        it_sum = float(st[3])
+        # algorithmic operations of the decode (as for the single-code leg)
+        it_host = iters.cpu().numpy().astype(np.int64)
+        ops = float(((OPS_PER_EDGE * edges_iter[cof] + OPS_PER_ROW *
+                      np.array([s.hbm.shape[0] * s.z for s in shapes])[cof]) * it_host).sum())
+        if dt == ldpc.I8X4:
+            ops /= 4.0
+        res[name] = {"value": info_bits * ws / (direct_ms * 1e-3) / 1e9, "unit": "Gbit/s",
+                     "ms": direct_ms,
+                     "graph_step": {"value": info_bits * ws / (graph_ms * 1e-3) / 1e9,
+                                    "ms": graph_ms,
+                                    "contents": ("quantise + " if dt == ldpc.I8X4 else "")
+                                    + f"{plan.n_groups} decode launches + error counting"},
+                     "per_code_launches": {"value": info_bits * ws / (pc_ms * 1e-3) / 1e9,
+                                           "ms": pc_ms, "launches": len(per_code)},
+                     "alg_tops": ops / (direct_ms * 1e-3) / 1e12,
+                     "fer": float(st[1]) / nf, "mean_iters": it_sum / nf,
+                     "autotune_seconds": tune_s, "groups": groups,
+                     "serial_groups": plan.serial()[name]}
+    return res
+
+
 def reference_arm(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -312,6 +421,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-frames", type=int, default=262144)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-frames", type=int, default=65536)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -488,6 +599,8 @@ def main():
 
     if not args.no_learned:
         res["learned"] = learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
+    if not args.no_mixed:
+        res["mixed"] = mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -278,8 +278,9 @@ void ldpc_codeset_destroy(ldpc_codeset *set);
  * frames are grouped by code (each code's run padded to a multiple of four
  * frames) and the codes are split into launch groups: one per slot class of
  * the largest row degree (8, 12, 16, 20, 24, 27), split further so that
- * shared memory within a group differs by at most a factor of two.  The set
- * must outlive the plan. */
+ * shared memory within a group differs by at most a factor of two, ordered
+ * by work (frames x edges), heaviest first.  The set must outlive the
+ * plan. */
 ldpc_status ldpc_mixed_plan_create(const ldpc_codeset *set, const int32_t *h_code_of_frame,
                                    int64_t frames, ldpc_mixed_plan **out);
 void ldpc_mixed_plan_destroy(ldpc_mixed_plan *plan);
@@ -302,6 +303,11 @@ ldpc_status ldpc_mixed_plan_offsets(const ldpc_mixed_plan *plan, int64_t *h_llr_
 ldpc_status ldpc_mixed_group_info(const ldpc_mixed_plan *plan, int group, int *slot_class,
                                   int *codes, int *smem_f32, int *smem_i8, int *chunk_f32,
                                   int *chunk_i8, int *blocks_per_sm_f32, int *blocks_per_sm_i8);
+
+/* Whether the plan launches its groups one after another on the caller's
+ * stream (1) or concurrently on forked streams (0), per dtype; the autotuner
+ * picks it.  Outputs may be NULL. */
+ldpc_status ldpc_mixed_plan_serial(const ldpc_mixed_plan *plan, int *serial_f32, int *serial_i8);
 
 /* int8 input of a mixed batch: each LLR quantised as in ldpc_quantize_pack_i8
  * (scale, clip) and packed four frames of the same code per word in the

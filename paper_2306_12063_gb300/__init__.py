@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
         "ldpc_mixed_plan_offsets": ([vp, vp, vp, vp], i32),
         "ldpc_mixed_group_info": ([vp, i32] + [P(i32)] * 8, i32),
         "ldpc_mixed_quantize": ([vp, vp, vp, f32, i32, vp], i32),
+        "ldpc_mixed_plan_serial": ([vp, P(i32), P(i32)], i32),
         "ldpc_decode_mixed": ([vp, i32, vp, P(_Params), vp, vp, vp, vp], i32),
         "ldpc_mixed_stats": ([vp, vp, vp, vp, i32, vp, vp, vp], i32),
         "ldpc_mixed_autotune": ([vp, i32, vp, P(_Params), vp, vp, i32, vp], i32),
@@ -400,6 +401,11 @@ class MixedPlan:
                     "blocks_per_sm_f32", "blocks_per_sm_i8")
             out.append(dict(zip(keys, [x.value for x in v])))
         return out
+
+    def serial(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().ldpc_mixed_plan_serial(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"fp32": bool(a.value), "int8": bool(b.value)}
 
     def _dev(self):
         return self.codeset.codes[0].device

@@ -78,9 +78,10 @@ __global__ void __launch_bounds__(32)
 }
 
 // One int8 launch: a work item's frames enter a packed word four at a time
-// and each byte lane is refilled from the item's remaining frames as soon as
-// its frame stops (as in the single-code kernel); the warp takes the next
-// item when all four lanes are idle.  ibase[c] is code c's first internal
+// and each byte lane is refilled as soon as its frame stops (as in the
+// single-code kernel), from the item's remaining frames and then from the
+// next items while they belong to the same code; an item of another code
+// waits until all four lanes are idle.  ibase[c] is code c's first internal
 // index, qoff[c] the word offset of its packed groups.
 template <int DMAX>
 __global__ void __launch_bounds__(32)
@@ -105,11 +106,12 @@ __global__ void __launch_bounds__(32)
     int64_t it = blockIdx.x;
     while (it < n_items) {
         const MixedItem item = items[it];
+        it = -1;   // no item fetched ahead yet
         const DevCode c = codes[item.code];
         const long long base = ibase[item.code];
         const uint32_t *qc = q + qoff[item.code];
         uint32_t *rows = Zs + ((c.n + 4) & ~3);
-        const long long end = item.start + item.count;
+        long long end = item.start + item.count;
         long long fr[4];
         int kb[4];
 #pragma unroll
@@ -149,6 +151,19 @@ __global__ void __launch_bounds__(32)
                 if (uf >= 0)
                     write_frame_i8_to(c, Zs, b, kb[b], hard + hard_off[uf], iters + uf,
                                       post ? post + llr_off[uf] : nullptr, lane);
+                if (next >= end && it < 0) {
+                    // this item is used up: take the next one; keep refilling
+                    // from it if it is of the same code
+                    it = next_work(work, gridDim.x, lane);
+                    if (it < n_items) {
+                        const MixedItem nx = items[it];
+                        if (nx.code == item.code) {
+                            next = nx.start;
+                            end = nx.start + nx.count;
+                            it = -1;
+                        }
+                    }
+                }
                 if (next >= end) {
                     fr[b] = -1;
                     continue;
@@ -169,7 +184,7 @@ __global__ void __launch_bounds__(32)
             }
         }
         __syncwarp();
-        it = next_work(work, gridDim.x, lane);
+        if (it < 0) it = next_work(work, gridDim.x, lane);
     }
 }
 
@@ -289,7 +304,8 @@ struct MixedPlan {
     int *d_group_code = nullptr;
     long long *d_group_first = nullptr, *d_group_qoff = nullptr;
     unsigned long long *d_work = nullptr;                // one counter per group and dtype
-    std::vector<MixedGroup> groups;
+    std::vector<MixedGroup> groups;     // heaviest (edges x frames) first
+    bool serial[2] = {false, false};     // groups one after another on the caller's stream
     cudaEvent_t fork = nullptr;
     std::mutex mu;                                       // item rebuilds
 };
@@ -418,9 +434,18 @@ static ldpc_status launch_group(MixedPlan &pl, int gi, int dt, const void *d_in,
     }
 }
 
-// All groups, forked from `s` onto the groups' streams and joined back.
+// All groups, forked from `s` onto the groups' streams and joined back (or,
+// when the plan says so, one after another on `s`).
 static ldpc_status launch_all(MixedPlan &pl, int dt, const void *d_in, const DecodeParams &p,
                               uint32_t *d_hard, int32_t *d_iters, void *d_post, cudaStream_t s) {
+    if (pl.serial[dt]) {
+        for (size_t gi = 0; gi < pl.groups.size(); ++gi) {
+            ldpc_status st = launch_group(pl, static_cast<int>(gi), dt, d_in, p, d_hard, d_iters,
+                                          d_post, s);
+            if (st != LDPC_OK) return st;
+        }
+        return LDPC_OK;
+    }
     cudaError_t e = cudaEventRecord(pl.fork, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed fork");
     for (size_t gi = 0; gi < pl.groups.size(); ++gi) {
@@ -583,6 +608,20 @@ ldpc_status ldpc_mixed_plan_create(const ldpc_codeset *set, const int32_t *h_cod
         if (c.n % 4) g.bulk_ok = false;
         if (!all_n4) g.bulk_ok = false;
     }
+    // heaviest groups first: their launches start first and the lighter ones
+    // fill the SMs as the heavy queues drain
+    {
+        auto work_of = [&](const MixedGroup &g) {
+            double w = 0;
+            for (int ci : g.codes)
+                w += static_cast<double>(pl->fcount[ci]) * codes[ci]->n_edges * codes[ci]->z;
+            return w;
+        };
+        std::stable_sort(pl->groups.begin(), pl->groups.end(),
+                         [&](const MixedGroup &a, const MixedGroup &b) {
+                             return work_of(a) > work_of(b);
+                         });
+    }
     // internal order, packed int8 groups
     pl->ibase.assign(count, 0);
     pl->qoff.assign(count, 0);
@@ -744,6 +783,14 @@ ldpc_status stats_mixed(const MixedPlan &p, const uint8_t *d_info, const uint32_
 
 extern "C" {
 
+ldpc_status ldpc_mixed_plan_serial(const ldpc_mixed_plan *plan, int *serial_f32,
+                                   int *serial_i8) {
+    if (!plan) return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_plan_serial: plan is NULL");
+    if (serial_f32) *serial_f32 = plan->p->serial[0] ? 1 : 0;
+    if (serial_i8) *serial_i8 = plan->p->serial[1] ? 1 : 0;
+    return LDPC_OK;
+}
+
 ldpc_status ldpc_mixed_quantize(const ldpc_mixed_plan *plan, const float *d_llr, uint32_t *d_q,
                                 float scale, int clip, cudaStream_t stream) {
     if (!plan) return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_quantize: plan is NULL");
@@ -851,6 +898,13 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
             if (ms < best) best = ms;
             else g.per_sm[dt] = old;
         }
+    }
+    // concurrent groups (forked streams) or one after another
+    if (st == LDPC_OK && p.groups.size() > 1) {
+        p.serial[dt] = !p.serial[dt];
+        float ms = 0;
+        st = measure(&ms);
+        if (st == LDPC_OK && !(ms < best)) p.serial[dt] = !p.serial[dt];
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
