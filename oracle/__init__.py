@@ -75,6 +75,12 @@ def lib():
             L.ldpc_ref_sincos_turn.restype = None
             L.ldpc_ref_awgn_llr.argtypes = [vp, i64, i64, i32, u64, f32, f32, vp]
             L.ldpc_ref_quantize_i8.argtypes = [vp, vp, i64, f32, i32]
+            L.ldpc_ref_quantize_i16.argtypes = [vp, vp, i64, f32, i32]
+            L.ldpc_ref_decode_layered_i16w.argtypes = [vp, vp, i64, ctypes.POINTER(_Params),
+                                                       vp, vp, vp, ctypes.POINTER(i64)]
+            L.ldpc_ref_encode_bitmap.argtypes = [vp, vp, vp, i64]
+            L.ldpc_ref_rotate_block.argtypes = [vp, i32, i32, vp]
+            L.ldpc_ref_rotate_block.restype = None
             for name in ("ldpc_ref_decode_layered_f32",
                          "ldpc_ref_decode_flooding_f32"):
                 getattr(L, name).argtypes = [vp, vp, i64,
@@ -190,6 +196,26 @@ class RefCode:
             _ptr(post)), "ldpc_ref_decode_flooding_f32")
         return hard, iters, post
 
+    def decode_layered_i16w(self, llr_q, max_iters=10, normalise=False,
+                            early_stop=False, want_post=True):
+        """Section 5 int16 wrap-around decoder: (hard, iters, post, wrap events)."""
+        llr, F, hard, iters, post, p = self._decode(
+            None, llr_q, np.int16, max_iters, 0.75, normalise, early_stop,
+            want_post, np.int16)
+        ev = ctypes.c_int64(0)
+        _check(lib().ldpc_ref_decode_layered_i16w(
+            self._h, _ptr(llr), F, ctypes.byref(p), _ptr(hard), _ptr(iters),
+            _ptr(post), ctypes.byref(ev)), "ldpc_ref_decode_layered_i16w")
+        return hard, iters, post, int(ev.value)
+
+    def encode_bitmap(self, info_words: np.ndarray) -> np.ndarray:
+        """Alg. A1 bitmap encoder: u32[F][K/32] -> u32[F][N/32] (Z % 32 == 0)."""
+        w = np.ascontiguousarray(info_words, dtype=np.uint32).reshape(-1, self.k // 32)
+        out = np.zeros((w.shape[0], self.n // 32), dtype=np.uint32)
+        _check(lib().ldpc_ref_encode_bitmap(self._h, _ptr(w), _ptr(out), w.shape[0]),
+               "ldpc_ref_encode_bitmap")
+        return out
+
     def decode_layered_i8(self, llr_q, max_iters=10, normalise=True,
                           early_stop=False, want_post=True
                           ) -> Tuple[np.ndarray, np.ndarray, np.ndarray, int]:
@@ -201,6 +227,23 @@ class RefCode:
             self._h, _ptr(llr), F, ctypes.byref(p), _ptr(hard), _ptr(iters),
             _ptr(post), ctypes.byref(ev)), "ldpc_ref_decode_layered_i8")
         return hard, iters, post, int(ev.value)
+
+
+def quantize_i16(llr: np.ndarray, scale: float = 16.0, qb: int = 10) -> np.ndarray:
+    """Section 5 channel: rint(clamp(scale * llr, +-(2^qb - 1))) as int16."""
+    x = np.ascontiguousarray(llr, dtype=np.float32)
+    out = np.zeros(x.shape, dtype=np.int16)
+    _check(lib().ldpc_ref_quantize_i16(_ptr(x), _ptr(out), x.size, float(scale), int(qb)),
+           "ldpc_ref_quantize_i16")
+    return out
+
+
+def rotate_block(words: np.ndarray, s: int) -> np.ndarray:
+    """P_s on one packed block (Alg. A1 split)."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    out = np.zeros_like(w)
+    lib().ldpc_ref_rotate_block(_ptr(w), int(w.size), int(s), _ptr(out))
+    return out
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -645,6 +645,159 @@ int ldpc_ref_decode_flooding_f32(const ldpc_ref_code *c, const float *llr,
     return LDPC_REF_OK;
 }
 
+/* ---------------------------------------------------------------------------
+ * Section 5: int16 fixed point with wrap-around arithmetic.
+ * ------------------------------------------------------------------------- */
+int ldpc_ref_quantize_i16(const float *llr, int16_t *q, int64_t count, float scale,
+                          int qb) {
+    if ((!llr && count) || (!q && count) || count < 0 || qb < 1 || qb > 14)
+        return LDPC_REF_ERR_INVALID_ARG;
+    const float lim = (float)((1 << qb) - 1);
+    for (int64_t i = 0; i < count; i++) {
+        float v = scale * llr[i];
+        if (v > lim) v = lim;
+        if (v < -lim) v = -lim;
+        q[i] = (int16_t)nearbyintf(v);   /* default rounding: half to even */
+    }
+    return LDPC_REF_OK;
+}
+
+/* x reduced modulo 2^16 into [-32768, 32767], counting changes. */
+static int wrap16(int x, int64_t *events) {
+    int y = x & 0xFFFF;
+    if (y >= 32768) y -= 65536;
+    if (y != x) (*events)++;
+    return y;
+}
+
+int ldpc_ref_decode_layered_i16w(const ldpc_ref_code *c, const int16_t *llr,
+                                 int64_t frames, const ldpc_ref_params *p,
+                                 uint32_t *hard, int32_t *iters, int16_t *post,
+                                 int64_t *wrap_events) {
+    int st = check_params(c, p, frames, llr, hard, iters);
+    if (st) return st;
+    if (p->normalise && p->alpha != 0.75f) return LDPC_REF_ERR_UNSUPPORTED;
+    const int n = c->n, nw = (n + 31) / 32;
+    int *Zn = (int *)malloc(sizeof(int) * n);
+    int *L = (int *)malloc(sizeof(int) * (c->nnz ? c->nnz : 1));
+    int *Q = (int *)malloc(sizeof(int) * (c->max_deg ? c->max_deg : 1));
+    int *A = (int *)malloc(sizeof(int) * (c->max_deg ? c->max_deg : 1));
+    int *Ln = (int *)malloc(sizeof(int) * (c->max_deg ? c->max_deg : 1));
+    uint8_t *bits = (uint8_t *)malloc(n);
+    if (!Zn || !L || !Q || !A || !Ln || !bits) {
+        free(Zn); free(L); free(Q); free(A); free(Ln); free(bits);
+        return LDPC_REF_ERR_NOMEM;
+    }
+    int64_t events = 0;
+    for (int64_t f = 0; f < frames; f++) {
+        for (int v = 0; v < n; v++) Zn[v] = llr[f * (int64_t)n + v];
+        for (int e = 0; e < c->nnz; e++) L[e] = 0;
+        int done = p->max_iters;
+        for (int k = 1; k <= p->max_iters; k++) {
+            for (int i = 0; i < c->mb; i++) {
+                for (int r = 0; r < c->z; r++) {
+                    int row = i * c->z + r;
+                    int b = c->row_start[row];
+                    int d = c->row_start[row + 1] - b;
+                    for (int t = 0; t < d; t++) {                      /* eq. (22) */
+                        Q[t] = wrap16(Zn[c->row_var[b + t]] - L[b + t], &events);
+                        A[t] = wrap16(Q[t] < 0 ? -Q[t] : Q[t], &events);   /* |Z_mn| */
+                    }
+                    for (int t = 0; t < d; t++) {                      /* eq. (23) */
+                        int mn = 1 << 30, neg = 0;
+                        for (int u = 0; u < d; u++) {
+                            if (u == t) continue;
+                            if (A[u] < mn) mn = A[u];
+                            if (Q[u] < 0) neg ^= 1;
+                        }
+                        if (p->normalise) mn = wrap16((3 * mn) >> 2, &events);
+                        Ln[t] = neg ? wrap16(-mn, &events) : mn;
+                    }
+                    for (int t = 0; t < d; t++) {                      /* eq. (20) */
+                        L[b + t] = Ln[t];
+                        Zn[c->row_var[b + t]] = wrap16(Q[t] + Ln[t], &events);
+                    }
+                }
+            }
+            if (p->early_stop) {
+                hard_from_int(Zn, n, hard + f * (int64_t)nw, bits);
+                if (ldpc_ref_syndrome_weight(c, bits) == 0) { done = k; break; }
+            }
+        }
+        hard_from_int(Zn, n, hard + f * (int64_t)nw, bits);
+        iters[f] = done;
+        if (post) for (int v = 0; v < n; v++) post[f * (int64_t)n + v] = (int16_t)Zn[v];
+    }
+    if (wrap_events) *wrap_events = events;
+    free(Zn); free(L); free(Q); free(A); free(Ln); free(bits);
+    return LDPC_REF_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Section 3: bitmap encoder.  A packed block of Z = 32 zw bits, bit r at bit
+ * r % 32 of word r / 32.  P_s (out bit r = in bit (r + s) mod Z) splits, as
+ * in Alg. A1, into sw = s / 32 whole words and sb = s % 32 bits: output word
+ * w takes the top 32 - sb bits of input word (w + sw) mod zw (shifted down)
+ * and the low sb bits of the next input word (shifted up).
+ * ------------------------------------------------------------------------- */
+void ldpc_ref_rotate_block(const uint32_t *in, int zw, int s, uint32_t *out) {
+    const int sw = s / 32, sb = s % 32;
+    for (int w = 0; w < zw; w++) {
+        uint32_t lo = in[(w + sw) % zw];
+        uint32_t hi = in[(w + sw + 1) % zw];
+        out[w] = sb ? (lo >> sb) | (hi << (32 - sb)) : lo;
+    }
+}
+
+int ldpc_ref_encode_bitmap(const ldpc_ref_code *c, const uint32_t *info, uint32_t *cw,
+                           int64_t frames) {
+    if (!c || (!info && frames) || (!cw && frames) || frames < 0)
+        return LDPC_REF_ERR_INVALID_ARG;
+    if (!c->encodable) return LDPC_REF_ERR_BAD_STRUCTURE;
+    if (c->z % 32) return LDPC_REF_ERR_UNSUPPORTED;
+    const int zw = c->z / 32, mb = c->mb, nb = c->nb, kb = c->kb;
+    uint32_t *S = (uint32_t *)malloc(sizeof(uint32_t) * mb * zw);
+    uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * zw);
+    uint32_t *sum = (uint32_t *)malloc(sizeof(uint32_t) * zw);
+    if (!S || !tmp || !sum) { free(S); free(tmp); free(sum); return LDPC_REF_ERR_NOMEM; }
+    for (int64_t f = 0; f < frames; f++) {
+        const uint32_t *u = info + f * (int64_t)(kb * zw);
+        uint32_t *out = cw + f * (int64_t)(nb * zw);
+        for (int w = 0; w < kb * zw; w++) out[w] = u[w];
+        uint32_t *v = out + kb * zw;
+        for (int i = 0; i < mb; i++) {                   /* eq. (15) */
+            uint32_t *Si = S + i * zw;
+            for (int w = 0; w < zw; w++) Si[w] = 0;
+            for (int j = 0; j < kb; j++) {
+                int s = c->hbm[i * nb + j];
+                if (s < 0) continue;
+                ldpc_ref_rotate_block(u + j * zw, zw, s, tmp);
+                for (int w = 0; w < zw; w++) Si[w] ^= tmp[w];
+            }
+        }
+        for (int w = 0; w < zw; w++) sum[w] = 0;        /* eq. (12) */
+        for (int i = 0; i < mb; i++)
+            for (int w = 0; w < zw; w++) sum[w] ^= S[i * zw + w];
+        {
+            int b = c->hbm[c->y * nb + kb];             /* P_b^{-1} = P_{Z-b} */
+            ldpc_ref_rotate_block(sum, zw, (c->z - b) % c->z, v);
+        }
+        ldpc_ref_rotate_block(v, zw, c->hbm[kb], v + zw);   /* eq. (13) */
+        for (int w = 0; w < zw; w++) v[zw + w] ^= S[w];
+        for (int i = 1; i < mb - 1; i++) {                   /* eq. (14) */
+            uint32_t *vn = v + (i + 1) * zw;
+            for (int w = 0; w < zw; w++) vn[w] = v[i * zw + w] ^ S[i * zw + w];
+            int s = c->hbm[i * nb + kb];
+            if (s >= 0) {
+                ldpc_ref_rotate_block(v, zw, s, tmp);
+                for (int w = 0; w < zw; w++) vn[w] ^= tmp[w];
+            }
+        }
+    }
+    free(S); free(tmp); free(sum);
+    return LDPC_REF_OK;
+}
+
 /* Index of the first nonzero block of H_bm block row i in row-major order. */
 static int block_edge_base(const ldpc_ref_code *c, int i) {
     int q = 0;

@@ -120,6 +120,35 @@ int ldpc_ref_decode_flooding_f32(const ldpc_ref_code *code, const float *llr,
                                  int64_t frames, const ldpc_ref_params *p,
                                  uint32_t *hard, int32_t *iters, float *post);
 
+/* Section 5's fixed-point channel: q = rint(clamp(scale * llr, -(2^qb - 1),
+ * 2^qb - 1)), round half to even, stored in int16 (qb = 10: -1023..1023). */
+int ldpc_ref_quantize_i16(const float *llr, int16_t *q, int64_t count,
+                          float scale, int qb);
+/* The layered decoder in Section 5's int16 arithmetic with native wrap-around
+ * (no saturation): every Z_mn and Z_n write, every |Z_mn| and every message
+ * is reduced modulo 2^16 into [-32768, 32767] (so |-32768| = -32768, the
+ * smallest value under the signed comparisons of the minimum).  normalise
+ * means m -> (3 m) >> 2 (arithmetic shift) and requires alpha == 0.75.
+ * wrap_events (or NULL) receives the number of reductions that changed a
+ * value. */
+int ldpc_ref_decode_layered_i16w(const ldpc_ref_code *code, const int16_t *llr,
+                                 int64_t frames, const ldpc_ref_params *p,
+                                 uint32_t *hard, int32_t *iters, int16_t *post,
+                                 int64_t *wrap_events);
+
+/* Bitmap encoder (Section 3, Alg. A1) for Z a multiple of 32: the direct
+ * encoder of eq. (12)-(15) on packed words, bit r of block j at bit
+ * (j Z + r) % 32 of word (j Z + r) / 32 (LSB first).  Each cyclic shift
+ * P_s is split as in Alg. A1 into a rotation by sw = s / 32 whole words and
+ * sb = s % 32 bits, the two combined in one pass over the block's words.
+ * info u32[frames][K/32] -> cw u32[frames][N/32]; Z % 32 != 0 gives
+ * LDPC_REF_ERR_UNSUPPORTED. */
+int ldpc_ref_encode_bitmap(const ldpc_ref_code *code, const uint32_t *info,
+                           uint32_t *cw, int64_t frames);
+/* out = P_s in on one packed block of zw = Z/32 words (the rotation used by
+ * ldpc_ref_encode_bitmap): out bit r = in bit (r + s) mod Z. */
+void ldpc_ref_rotate_block(const uint32_t *in, int zw, int s, uint32_t *out);
+
 #ifdef __cplusplus
 }
 #endif
