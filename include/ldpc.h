@@ -48,9 +48,15 @@ typedef enum {
 
 typedef enum {
     LDPC_F32 = 0,   /* channel LLRs float[F][N]; posteriors float[F][N] */
-    LDPC_I8X4 = 1   /* channel LLRs int8 packed four frames per 32-bit word,
+    LDPC_I8X4 = 1,  /* channel LLRs int8 packed four frames per 32-bit word,
                        uint32[ceil(F/4)][N], byte b of word (g, n) = frame
                        4g + b; posteriors int8[F][N] */
+    LDPC_I16W = 2   /* Section 5's fixed-point decoder: channel int16[F][N]
+                       (ldpc_quantize_i16), int16 arithmetic with native
+                       wrap-around (every Z_mn, |Z_mn|, message and Z_n is
+                       reduced modulo 2^16 into [-32768, 32767], so
+                       |-32768| = -32768); posteriors int16[F][N].  Only
+                       ldpc_decode_layered_minsum takes it. */
 } ldpc_dtype;
 
 typedef struct ldpc_code ldpc_code;   /* opaque; created and freed here */
@@ -110,6 +116,23 @@ ldpc_status ldpc_awgn_llr(const uint8_t *d_code, int64_t frame0, int64_t frames,
                           int n, uint64_t seed, float sigma, float llr_scale,
                           float *d_llr, cudaStream_t stream);
 
+/* Section 5's fixed-point channel: q = rint(clamp(scale * llr, -(2^qb - 1),
+ * 2^qb - 1)) with round-half-to-even, stored as int16 (Q_B = qb; the paper's
+ * default qb = 10 gives -1023..1023).  d_llr float[count] -> d_q int16[count];
+ * 1 <= qb <= 14. */
+ldpc_status ldpc_quantize_i16(const float *d_llr, int16_t *d_q, int64_t count, float scale,
+                              int qb, cudaStream_t stream);
+
+/* Bitmap encoder (Section 3, Alg. A1), for Z a multiple of 32: the direct
+ * encoder of eq. (12)-(15) on packed words.  Bit r of block j sits at bit
+ * (j Z + r) % 32 of word (j Z + r) / 32; each cyclic shift P_s (out bit r =
+ * in bit (r + s) mod Z) is split as in Alg. A1 into s / 32 whole words and
+ * s % 32 bits, combined in one pass over the block.  d_info
+ * uint32[frames][K/32] -> d_code uint32[frames][N/32].  Z % 32 != 0 gives
+ * LDPC_ERR_UNSUPPORTED. */
+ldpc_status ldpc_encode_bitmap(const ldpc_code *code, const uint32_t *d_info, uint32_t *d_code,
+                               int64_t frames, cudaStream_t stream);
+
 /* Fixed-point channel input (Section 5, narrowed to 8 bits):
  * q = rint(clamp(scale * llr, -clip, clip)) with round-half-to-even, packed
  * four frames per word: d_llr float[frames][n] -> d_q uint32[ceil(frames/4)][n],
@@ -164,6 +187,21 @@ ldpc_status ldpc_decode_learned_minsum(const ldpc_code *code, const float *d_llr
                                        int64_t frames, const float *d_weights, int T,
                                        int early_stop, uint32_t *d_hard, int32_t *d_iters,
                                        float *d_post, cudaStream_t stream);
+
+/* Flooding min-sum (Section 4, eq. 18-21) in FP32, the schedule the layered
+ * decoder improves on: each iteration first computes every check message
+ * from the previous iteration's messages, Z_mn = Z_n^(0) + sum over the
+ * variable's other checks of L (eq. 19, summed in increasing check index),
+ * L_mn = s * min over the row's other edges of |Z_mn'| * their sign product
+ * (eq. 18; s = alpha if normalise, else 1), then every posterior
+ * Z_n = Z_n^(0) + sum of its L (eq. 20, increasing check index), and the
+ * syndrome stop (eq. 21).  Arguments as for ldpc_decode_layered_minsum with
+ * LDPC_F32.  Shared memory per frame is 4 (2 N + 2 nnz(H)) bytes; larger
+ * codes return LDPC_ERR_UNSUPPORTED. */
+ldpc_status ldpc_decode_flooding_minsum(const ldpc_code *code, const float *d_llr,
+                                        int64_t frames, const ldpc_decode_params *params,
+                                        uint32_t *d_hard, int32_t *d_iters, float *d_post,
+                                        cudaStream_t stream);
 
 /* Device workspace bytes of ldpc_decode_learned_fallback for `frames`. */
 size_t ldpc_learned_fallback_workspace_bytes(const ldpc_code *code, int64_t frames);

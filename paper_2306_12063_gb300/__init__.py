@@ -18,10 +18,11 @@ from . import _build
 
 __all__ = ["LdpcError", "Code", "load", "gen_info", "awgn_llr", "quantize_pack_i8",
            "awgn_llr_frames", "snr_sigma", "adam_step", "CodeSet", "MixedPlan", "MixedGraph",
-           "F32", "I8X4", "symbols"]
+           "quantize_i16", "F32", "I8X4", "I16W", "symbols"]
 
 F32 = 0
 I8X4 = 1
+I16W = 2
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_STRUCTURE", 3: "NOMEM", 4: "CUDA",
            5: "TIMEOUT", 6: "UNSUPPORTED"}
@@ -108,6 +109,9 @@ def load(build_if_missing: bool = False):
                                      P(vp)], i32),
         "ldpc_mixed_graph_launch": ([vp, vp], i32),
         "ldpc_mixed_graph_destroy": ([vp], None),
+        "ldpc_quantize_i16": ([vp, vp, i64, f32, i32, vp], i32),
+        "ldpc_encode_bitmap": ([vp, vp, vp, i64, vp], i32),
+        "ldpc_decode_flooding_minsum": ([vp, vp, i64, P(_Params), vp, vp, vp, vp], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -185,12 +189,13 @@ class Code:
     def decode(self, llr, frames: Optional[int] = None, dtype: int = F32, max_iters: int = 10,
                alpha: float = 0.75, normalise: bool = True, early_stop: bool = False,
                want_post: bool = False, out=None, stream=None):
-        """Layered min-sum (Section 4).  llr: float32[F][N] (F32) or the packed
-        int32/uint32 [ceil(F/4)][N] words of quantize_pack_i8 (I8X4).
+        """Layered min-sum (Section 4).  llr: float32[F][N] (F32), the packed
+        int32/uint32 [ceil(F/4)][N] words of quantize_pack_i8 (I8X4), or
+        int16[F][N] from quantize_i16 (I16W, Section 5 wrap-around).
         Returns (hard int32[F][ceil(N/32)], iters int32[F], post or None)."""
         torch = _torch()
         if frames is None:
-            frames = llr.shape[0] if dtype == F32 else 4 * llr.shape[0]
+            frames = 4 * llr.shape[0] if dtype == I8X4 else llr.shape[0]
         dev = llr.device
         if out is None:
             hard = torch.empty((frames, self.nwords), dtype=torch.int32, device=dev)
@@ -198,7 +203,8 @@ class Code:
             post = None
             if want_post:
                 post = torch.empty((frames, self.n),
-                                   dtype=torch.float32 if dtype == F32 else torch.int8,
+                                   dtype={F32: torch.float32, I8X4: torch.int8,
+                                          I16W: torch.int16}[dtype],
                                    device=dev)
         else:
             hard, iters, post = out
@@ -206,6 +212,33 @@ class Code:
         _check(load().ldpc_decode_layered_minsum(self._h, int(dtype), _ptr(llr), int(frames),
                                                  ctypes.byref(p), _ptr(hard), _ptr(iters),
                                                  _ptr(post), _stream(stream)))
+        return hard, iters, post
+
+    def encode_bitmap(self, info_words, out=None, stream=None):
+        """Alg. A1 bitmap encoder (Z % 32 == 0): uint32/int32[F][K/32] packed
+        info -> [F][N/32] packed codeword."""
+        torch = _torch()
+        F = info_words.shape[0]
+        if out is None:
+            out = torch.empty((F, self.n // 32), dtype=torch.int32, device=info_words.device)
+        _check(load().ldpc_encode_bitmap(self._h, _ptr(info_words), _ptr(out), int(F),
+                                         _stream(stream)))
+        return out
+
+    def decode_flooding(self, llr, max_iters: int = 10, alpha: float = 0.75,
+                        normalise: bool = True, early_stop: bool = False,
+                        want_post: bool = False, stream=None):
+        """Flooding min-sum (eq. 18-21), FP32."""
+        torch = _torch()
+        F = llr.shape[0]
+        hard = torch.empty((F, self.nwords), dtype=torch.int32, device=llr.device)
+        iters = torch.empty((F,), dtype=torch.int32, device=llr.device)
+        post = (torch.empty((F, self.n), dtype=torch.float32, device=llr.device)
+                if want_post else None)
+        p = _Params(int(max_iters), float(alpha), int(bool(normalise)), int(bool(early_stop)))
+        _check(load().ldpc_decode_flooding_minsum(self._h, _ptr(llr), int(F), ctypes.byref(p),
+                                                  _ptr(hard), _ptr(iters), _ptr(post),
+                                                  _stream(stream)))
         return hard, iters, post
 
     @property
@@ -521,6 +554,16 @@ def awgn_llr(cw, frame0: int, seed: int, sigma: float, llr_scale: Optional[float
         out = torch.empty((F, n), dtype=torch.float32, device=cw.device)
     _check(load().ldpc_awgn_llr(_ptr(cw), int(frame0), int(F), int(n), int(seed), float(sig),
                                 float(llr_scale), _ptr(out), _stream(stream)))
+    return out
+
+
+def quantize_i16(llr, scale: float = 16.0, qb: int = 10, out=None, stream=None):
+    """Section 5 channel: float32[...] -> int16 rint(clamp(scale * llr, +-(2^qb - 1)))."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(llr.shape, dtype=torch.int16, device=llr.device)
+    _check(load().ldpc_quantize_i16(_ptr(llr), _ptr(out), int(llr.numel()), float(scale),
+                                    int(qb), _stream(stream)))
     return out
 
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libldpc.so")
 SOURCES = ["ldpc_api.cu", "ldpc_gen.cu", "ldpc_decode.cu", "ldpc_noalloc.cu", "ldpc_learned.cu",
-           "ldpc_train.cu", "ldpc_mixed.cu"]
+           "ldpc_train.cu", "ldpc_mixed.cu", "ldpc_variants.cu"]
 HEADERS = ["ldpc_internal.cuh", "ldpc_decode_dev.cuh", os.path.join("..", "..", "include", "ldpc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

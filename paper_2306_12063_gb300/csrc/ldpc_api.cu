@@ -79,6 +79,8 @@ static void release(Code &c) {
     cudaFree(c.d_rowinfo);
     cudaFree(c.d_edges);
     cudaFree(c.d_wgather);
+    cudaFree(c.d_colent);
+    cudaFree(c.d_coloff);
     cudaFree(c.d_status);
     cudaFree(c.d_work);
     for (auto &s : c.aux)
@@ -215,6 +217,22 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
             wgather[static_cast<size_t>(i) * wp + (D - d + e)] =
                 static_cast<int16_t>(c.layer_off[i] + e);
     }
+    // Column table: for each block column j, its nonzero blocks in increasing
+    // block row (the neighbourhood M(n) of every variable of the column).
+    std::vector<int> coloff(nb + 1, 0);
+    std::vector<uint32_t> colent;
+    for (int j = 0; j < nb; ++j) {
+        coloff[j] = static_cast<int>(colent.size());
+        for (int i = 0; i < mb; ++i) {
+            const int s = hbm[i * nb + j];
+            if (s < 0) continue;
+            int q = c.layer_off[i];
+            while (c.edge_col[q] != j) ++q;
+            colent.push_back((static_cast<uint32_t>(i) << 20) | (static_cast<uint32_t>(q) << 9) |
+                             static_cast<uint32_t>(s));
+        }
+    }
+    coloff[nb] = static_cast<int>(colent.size());
     std::vector<uint32_t> edges(c.n_edges);
     for (int q = 0; q < c.n_edges; ++q)
         edges[q] = (static_cast<uint32_t>(c.edge_col[q]) << 16) |
@@ -226,6 +244,8 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     if (e == cudaSuccess) e = cudaMalloc(&c.d_rowinfo, sizeof(uint32_t) * mb);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_edges, sizeof(uint32_t) * c.n_edges);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_wgather, sizeof(int16_t) * wgather.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_colent, sizeof(uint32_t) * colent.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_coloff, sizeof(int) * coloff.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c.d_work, sizeof(unsigned long long) * kWorkSlots);
     if (e == cudaSuccess)
@@ -241,6 +261,12 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c.d_wgather, wgather.data(), sizeof(int16_t) * wgather.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c.d_colent, colent.data(), sizeof(uint32_t) * colent.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c.d_coloff, coloff.data(), sizeof(int) * coloff.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c.d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -347,7 +373,7 @@ static ldpc_status check_decode_args(const ldpc_code *code, ldpc_dtype dtype, in
     std::string w(who);
     if (!code) return fail(LDPC_ERR_INVALID_ARG, w + ": code is NULL");
     if (!params) return fail(LDPC_ERR_INVALID_ARG, w + ": params is NULL");
-    if (dtype != LDPC_F32 && dtype != LDPC_I8X4)
+    if (dtype != LDPC_F32 && dtype != LDPC_I8X4 && dtype != LDPC_I16W)
         return fail(LDPC_ERR_INVALID_ARG, w + ": unknown dtype");
     if (frames < 0) return fail(LDPC_ERR_INVALID_ARG, w + ": frames < 0");
     if (params->max_iters < 1 || params->max_iters > kMaxIters)
@@ -358,9 +384,9 @@ static ldpc_status check_decode_args(const ldpc_code *code, ldpc_dtype dtype, in
         return fail(LDPC_ERR_INVALID_ARG, w + ": early_stop must be 0 or 1");
     if (params->normalise && !(params->alpha == params->alpha))
         return fail(LDPC_ERR_INVALID_ARG, w + ": alpha is NaN");
-    if (dtype == LDPC_I8X4 && params->normalise && params->alpha != 0.75f)
+    if (dtype != LDPC_F32 && params->normalise && params->alpha != 0.75f)
         return fail(LDPC_ERR_UNSUPPORTED,
-                    w + ": the int8 decoder scales by (3m)>>2, which needs alpha == 0.75");
+                    w + ": the integer decoders scale by (3m)>>2, which needs alpha == 0.75");
     if (code->c.max_deg > kMaxRowDeg)
         return fail(LDPC_ERR_UNSUPPORTED, w + ": row degree above 27");
     p->max_iters = params->max_iters;
@@ -383,6 +409,9 @@ ldpc_status ldpc_decode_layered_minsum(const ldpc_code *code, ldpc_dtype dtype,
         return fail(LDPC_ERR_INVALID_ARG, "ldpc_decode_layered_minsum: NULL buffer");
     st = bind(&code->c);
     if (st) return st;
+    if (dtype == LDPC_I16W)
+        return launch_decode_i16w(code->c, static_cast<const int16_t *>(d_llr), frames, p,
+                                  d_hard, d_iters, static_cast<int16_t *>(d_post), stream);
     return launch_decode(code->c, dtype, d_llr, frames, p, d_hard, d_iters, d_post, stream);
 }
 
@@ -439,6 +468,8 @@ ldpc_status ldpc_decode_host(const ldpc_code *code, ldpc_dtype dtype, const void
     DecodeParams p;
     ldpc_status st = check_decode_args(code, dtype, frames, params, &p, "ldpc_decode_host");
     if (st) return st;
+    if (dtype == LDPC_I16W)
+        return fail(LDPC_ERR_UNSUPPORTED, "ldpc_decode_host: LDPC_F32 or LDPC_I8X4 only");
     if (frames == 0) return LDPC_OK;
     if (!h_llr || !h_hard || !h_iters || !d_workspace)
         return fail(LDPC_ERR_INVALID_ARG, "ldpc_decode_host: NULL buffer");

@@ -45,6 +45,9 @@ struct Code {
     uint32_t *d_rowinfo = nullptr;   // [mb] layer degree and first edge
     uint32_t *d_edges = nullptr;     // [n_edges] (block column << 16) | shift
     int16_t *d_wgather = nullptr;    // [mb][(dslots + 3) & ~3] block edge of each slot, -1 unused
+    uint32_t *d_colent = nullptr;    // [n_edges] per block column, block rows increasing:
+                                     //   (block row << 20) | (block edge << 9) | shift
+    int *d_coloff = nullptr;         // [nb + 1] start of each block column in d_colent
     int *d_status = nullptr;         // device status word
     cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -69,6 +72,8 @@ struct DevCode {
     const uint32_t *rowinfo;  // [mb] (first_edge << 8) | degree
     const uint32_t *edges;    // [n_edges] (block column << 16) | shift
     const int16_t *wgather;   // [mb][(dslots + 3) & ~3] block edge of each slot, -1 unused
+    const uint32_t *colent;   // [n_edges] column entries (block row, block edge, shift)
+    const int *coloff;        // [nb + 1]
     int *status;
 };
 
@@ -77,7 +82,8 @@ inline DevCode dev_view(const Code &c) {
     d.n = c.n; d.k = c.k; d.m = c.m; d.z = c.z; d.mb = c.mb; d.nb = c.nb;
     d.kb = c.kb; d.y = c.y; d.nwords = (c.n + 31) / 32; d.rpl = c.rpl; d.dslots = c.dslots;
     d.n_edges = c.n_edges; d.hbm = c.d_hbm; d.voff = c.d_voff;
-    d.rowinfo = c.d_rowinfo; d.edges = c.d_edges; d.wgather = c.d_wgather; d.status = c.d_status;
+    d.rowinfo = c.d_rowinfo; d.edges = c.d_edges; d.wgather = c.d_wgather;
+    d.colent = c.d_colent; d.coloff = c.d_coloff; d.status = c.d_status;
     return d;
 }
 
@@ -124,6 +130,11 @@ unsigned long long *work_slot(const Code &c, cudaStream_t s);
 ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr,
                           int64_t frames, const DecodeParams &p, uint32_t *d_hard,
                           int32_t *d_iters, void *d_post, cudaStream_t s);
+
+// Section 5 int16 decoder with wrap-around arithmetic (ldpc_variants.cu).
+ldpc_status launch_decode_i16w(const Code &c, const int16_t *d_llr, int64_t frames,
+                               const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
+                               int16_t *d_post, cudaStream_t s);
 
 // Learned normalised min-sum (FP32): per-iteration, per-block-edge weights.
 ldpc_status launch_decode_learned(const Code &c, const float *d_llr, int64_t frames,

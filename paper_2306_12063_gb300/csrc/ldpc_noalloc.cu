@@ -186,6 +186,8 @@ extern "C" ldpc_status ldpc_decode_layered_minsum_noalloc(
     dc.rowinfo = reinterpret_cast<const uint32_t *>(scratch + kScratchRowInfo);
     dc.edges = nullptr;   // the plain decoders read only the offset table
     dc.wgather = nullptr;
+    dc.colent = nullptr;
+    dc.coloff = nullptr;
     dc.status = reinterpret_cast<int *>(scratch + 8);
     DecodeParams p;
     p.max_iters = params->max_iters;
