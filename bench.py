@@ -107,7 +107,7 @@ class ClockSampler:
 def kernel_source_digest() -> str:
     """sha256 (first 16 hex digits) of the decoder kernel sources."""
     h = hashlib.sha256()
-    for name in ("ldpc_decode.cu", "ldpc_internal.cuh"):
+    for name in ("ldpc_decode.cu", "ldpc_decode_dev.cuh", "ldpc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2306_12063_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,6 +377,74 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     return res
 
 
+def variants_leg(args, ldpc, torch, dev, stream, barrier, code, batch, pg):
+    """The paper's variants timed on the same inputs as the main decoders:
+    Section 5's int16 wrap-around decoder and the flooding schedule on the
+    4.0 dB batch of the N=1944 workload, and the Alg. A1 bitmap encoder
+    against the byte encoder on the Z=96, R=5/6 WiMAX-shaped code."""
+    steps = max(1, args.steps // 2)
+
+    def time_fn(fn):
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = a.elapsed_time(b) / steps
+        if pg is not None:
+            tt = torch.tensor([ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    F = batch.info.shape[0]
+    bits = F * code.k
+    out = {"workload": "N=1944 R=5/6 batch at 4.0 dB (" + str(F) + " frames), max 20 iterations, "
+                       "early stop; encoder: WiMAX-shaped N=2304 R=5/6 (Z=96), " + str(F) +
+                       " frames"}
+    q16 = ldpc.quantize_i16(batch.llr, 16.0, 10)
+    hard = torch.empty((F, code.nwords), dtype=torch.int32, device=dev)
+    iters = torch.empty((F,), dtype=torch.int32, device=dev)
+    ms = time_fn(lambda: code.decode(q16, dtype=ldpc.I16W, max_iters=MAX_ITERS, normalise=True,
+                                     early_stop=True, out=(hard, iters, None)))
+    st = code.frame_stats(batch.info, hard, iters, MAX_ITERS).cpu().numpy()
+    out["int16_wrap"] = {"value": bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms": ms,
+                         "fer": float(st[1]) / F, "mean_iters": float(st[3]) / F,
+                         "quantiser": "rint(clamp(16 LLR, +-1023)), Q_B = 10",
+                         "normalise": "(3m)>>2"}
+    fl = {}
+
+    def flood():
+        fl["r"] = code.decode_flooding(batch.llr, MAX_ITERS, 0.75, True, True)
+
+    ms = time_fn(flood)
+    fh, fi, _ = fl["r"]
+    st = code.frame_stats(batch.info, fh, fi, MAX_ITERS).cpu().numpy()
+    out["flooding_f32"] = {"value": bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms": ms,
+                           "fer": float(st[1]) / F, "mean_iters": float(st[3]) / F}
+    sh = synth.wimax_n2304_r56()
+    ec = ldpc.Code(sh.hbm, sh.z, device=dev)
+    info = ldpc.gen_info(5, 0, F, ec.k, device=dev)
+    words = torch.from_numpy(np.packbits(info.cpu().numpy().reshape(F, ec.k // 8, 8), axis=2,
+                                         bitorder="little").reshape(F, ec.k // 8)
+                             .view(np.int32)).to(dev)
+    cwb = torch.empty((F, ec.n // 32), dtype=torch.int32, device=dev)
+    cw = torch.empty((F, ec.n), dtype=torch.uint8, device=dev)
+    ms_b = time_fn(lambda: ec.encode_bitmap(words, out=cwb))
+    ms_y = time_fn(lambda: ec.encode(info, out=cw))
+    out["encoder_bitmap"] = {"value": F * ec.k / (ms_b * 1e-3) / 1e9, "unit": "Gbit/s",
+                             "ms": ms_b, "hbm_gbs": F * (ec.k + ec.n) / 8 / (ms_b * 1e-3) / 1e9}
+    out["encoder_bytes"] = {"value": F * ec.k / (ms_y * 1e-3) / 1e9, "unit": "Gbit/s",
+                            "ms": ms_y, "hbm_gbs": F * (ec.k + ec.n) / (ms_y * 1e-3) / 1e9}
+    return out
+
+
 def reference_arm(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -415,13 +483,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=262144, help="frames per Eb/N0 batch")
-    ap.add_argument("--ref-frames", type=int, default=16384)
+    ap.add_argument("--ref-frames", type=int, default=32768,
+                    help="frames per step of the CPU reference arm")
+    ap.add_argument("--cpu-baseline-frames", type=int, default=262144,
+                    help="frames of the CPU-baseline sample (the whole 4.0 dB batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-frames", type=int, default=262144)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--mixed-frames", type=int, default=65536)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -601,14 +673,18 @@ def main():
         res["learned"] = learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
     if not args.no_mixed:
         res["mixed"] = mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
+    if not args.no_variants and not args.no_fp32:
+        res["variants"] = variants_leg(args, ldpc, torch, dev, stream, barrier, code, batches[1],
+                                       pg)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        bits, secs = run_oracle_sample(args.ref_frames, 4.0, threads)
+        nf = args.cpu_baseline_frames
+        bits, secs = run_oracle_sample(nf, 4.0, threads)
         cpu = {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": threads,
-               "kind": "oracle",
-               "sample": f"{args.ref_frames} frames of the 4.0 dB batch, int8, max 20 "
+               "kind": "oracle", "seconds": secs,
+               "sample": f"{nf} frames of the 4.0 dB batch, int8, max 20 "
                          f"iterations, early stop, {threads} threads, blocks of 10 frames"}
 
     if rank == 0:
