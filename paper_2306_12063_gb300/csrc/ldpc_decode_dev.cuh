@@ -64,12 +64,14 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 
 
 // ---------------------------------------------------------------------------
-// Row processing.  Every row runs all DMAX edge slots as straight-line code
-// (so the compiler can interleave the slots freely); a layer of degree d uses
-// slots DMAX-d .. DMAX-1 and the leading slots read a dummy posterior (word N
-// of the posterior array) whose value leaves the row's minimum, second
-// minimum, sign parity and syndrome unchanged.  Stores are made only for the
-// real slots.
+// Row processing.  Every row runs all DMAX edge slots of its instance as
+// straight-line code (so the compiler can interleave the slots freely); a
+// layer of degree d uses slots DMAX-d .. DMAX-1 and the leading slots read a
+// dummy posterior (word N of the posterior array) whose value leaves the
+// row's minimum, second minimum, sign parity and syndrome unchanged.  Stores
+// are made only for the real slots.  DS is the kernel's slot class (the
+// offset-table and row-state layout); DMAX <= DS the slots this instance
+// processes.
 // ---------------------------------------------------------------------------
 
 // FP32 layer: eq. (22) Z_mn = Z_n - L_mn; eq. (23) new L_mn from the
@@ -89,18 +91,17 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 // slot on the signed message.
 __host__ __device__ constexpr int wpad(int dmax) { return (dmax + 3) & ~3; }
 
-template <int DMAX, bool WT = false>
-__device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t *Zs,
+template <int DS, int DMAX, bool WT = false>
+__device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, uint32_t *Zs,
                                           uint32_t *rows, int lane, bool norm, float alpha,
                                           const float *wprev = nullptr,
                                           const float *wcur = nullptr) {
-    const uint32_t ri = __ldg(c.rowinfo + layer);
-    const int d = ri & 255;
     const int start = DMAX - d;
     float wp[WT ? wpad(DMAX) : 1], wc[WT ? wpad(DMAX) : 1];
     if (WT) {
-        const float4 *p4 = reinterpret_cast<const float4 *>(wprev);
-        const float4 *c4 = reinterpret_cast<const float4 *>(wcur);
+        // this layer's slots are the last DMAX of the DS staged ones
+        const float4 *p4 = reinterpret_cast<const float4 *>(wprev + (DS - DMAX));
+        const float4 *c4 = reinterpret_cast<const float4 *>(wcur + (DS - DMAX));
 #pragma unroll
         for (int j = 0; j < wpad(DMAX) / 4; ++j) {
             const float4 a = p4[j], b = c4[j];
@@ -117,7 +118,7 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
         const float m1 = __uint_as_float(rs[0]), m2 = __uint_as_float(rs[1]);
         const uint32_t meta = rs[2];
         const int idx = static_cast<int>(meta >> 27);
-        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
         uint32_t off[DMAX];
         float Q[DMAX];
 #pragma unroll
@@ -168,27 +169,66 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, uint32_t 
     }
 }
 
-// FP32 hard decision (eq. 21) and syndrome: true when every check holds.
-template <int DMAX>
+// Slots processed for a layer of degree d in a kernel built for DS slots: the
+// DS - 4 instance serves the layers that fit it (fewer padding slots), the
+// full instance the others.  Both read the same offset table (a row's real
+// edges occupy its last d slots) and keep their own row-state layout, since
+// a layer is always processed by the same instance.
+template <int DS>
+__host__ __device__ constexpr int sub_slots() { return DS >= 12 ? DS - 4 : (DS == 8 ? 4 : DS); }
+template <int DS>
+__device__ __forceinline__ bool use_sub(int d) { return sub_slots<DS>() < DS && d <= sub_slots<DS>(); }
+// The int8 row body is about twice the FP32 one; two large instances that
+// alternate from layer to layer no longer fit the instruction cache, so the
+// int8 kernels split only the small slot classes.
+template <int DS>
+__device__ __forceinline__ bool use_sub_i8(int d) { return DS <= 12 && use_sub<DS>(d); }
+
+// FP32 hard decision (eq. 21) and syndrome over the rows of one layer.
+template <int DS, int DMAX>
+__device__ __forceinline__ uint32_t syndrome_rows_f32(const DevCode &c, const uint32_t *Zs, int l,
+                                                      int lane) {
+    uint32_t bad = 0;
+    for (int t = 0; t < c.rpl; ++t) {
+        if (lane + 32 * t >= c.z) break;
+        const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
+        uint32_t off[DMAX];
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        uint32_t par = 0;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t u = lds_u32(Zs, off[i]);
+            par ^= (u - 1u) | u;   // bit 31 set iff Z <= 0 (negatives, -0 and +0)
+        }
+        bad |= par;
+    }
+    return bad;
+}
+
+// True when every check holds.
+template <int DS>
 __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t *Zs, int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
-        for (int t = 0; t < c.rpl; ++t) {
-            if (lane + 32 * t >= c.z) break;
-            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
-            uint32_t off[DMAX];
-#pragma unroll
-            for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
-            uint32_t par = 0;
-#pragma unroll
-            for (int i = 0; i < DMAX; ++i) {
-                const uint32_t u = lds_u32(Zs, off[i]);
-                par ^= (u - 1u) | u;   // bit 31 set iff Z <= 0 (negatives, -0 and +0)
-            }
-            bad |= par;
-        }
+        const int d = __ldg(c.rowinfo + l) & 255;
+        bad |= use_sub<DS>(d) ? syndrome_rows_f32<DS, sub_slots<DS>()>(c, Zs, l, lane)
+                              : syndrome_rows_f32<DS, DS>(c, Zs, l, lane);
     }
     return !__any_sync(kFull, bad >> 31);
+}
+
+// One FP32 layer through the instance that fits it.
+template <int DS, bool WT = false>
+__device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint32_t *Zs,
+                                              uint32_t *rows, int lane, bool norm, float alpha,
+                                              const float *wprev = nullptr,
+                                              const float *wcur = nullptr) {
+    const int d = __ldg(c.rowinfo + layer) & 255;
+    if (use_sub<DS>(d))
+        layer_f32<DS, sub_slots<DS>(), WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur);
+    else
+        layer_f32<DS, DS, WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur);
 }
 
 // ---------------------------------------------------------------------------
@@ -203,12 +243,10 @@ __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t
 // dummy posterior is +127 and the leading slots' stored message sign is
 // kept negative, so their Z_mn clamps to +127: never below a minimum.
 // ---------------------------------------------------------------------------
-template <int DMAX>
-__device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *Zs, uint32_t *rows,
-                                         int lane, bool norm) {
+template <int DS, int DMAX>
+__device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uint32_t *Zs,
+                                         uint32_t *rows, int lane, bool norm) {
     constexpr int SGW = sign_words(DMAX);
-    const uint32_t ri = __ldg(c.rowinfo + layer);
-    const int d = ri & 255;
     const int start = DMAX - d;
     // sign bits forced on for the leading (unused) slots, per sign word
     uint32_t pad[SGW];
@@ -220,7 +258,7 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
     for (int t = 0; t < c.rpl; ++t) {
         const int r = lane + 32 * t;
         if (r >= c.z) break;
-        uint32_t *rs = rows + (layer * c.z + r) * row_words_i8(DMAX);
+        uint32_t *rs = rows + (layer * c.z + r) * row_words_i8(DS);
         const uint32_t M1 = rs[0], M2 = rs[1], IDX = rs[2];
         uint32_t SG[SGW];
 #pragma unroll
@@ -228,7 +266,7 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, uint32_t *
         // offset-128 bytes of -L_old for the four (sign, magnitude) cases
         const uint32_t P1c = 0x80808080u - M1, P2c = 0x80808080u - M2;   // L > 0
         const uint32_t N1c = 0x80808080u | M1, N2c = 0x80808080u | M2;   // L < 0
-        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
         uint32_t off[DMAX], Q[DMAX];
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
@@ -299,28 +337,51 @@ __device__ __forceinline__ uint32_t hard_bytes_off(uint32_t u) {
     return ~(u - 0x01010101u) & 0x80808080u;   // u >= 1: no borrow crosses bytes
 }
 
+// int8 syndrome over the rows of one layer: bit 7 of byte b set when frame b
+// has an unsatisfied check there.
+template <int DS, int DMAX>
+__device__ __forceinline__ uint32_t syndrome_rows_i8(const DevCode &c, const uint32_t *Zs, int l,
+                                                     int lane) {
+    uint32_t bad = 0;
+    for (int t = 0; t < c.rpl; ++t) {
+        if (lane + 32 * t >= c.z) break;
+        const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
+        uint32_t off[DMAX];
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        // bit 7 of (u - 1) is set iff Z >= 1, so each of the DMAX terms (the
+        // dummy +127 ones included) flips the parity of the hard decisions
+        uint32_t par = (DMAX & 1) ? 0x80808080u : 0u;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i)
+            par ^= lds_u32(Zs, off[i]) - 0x01010101u;   // bytes >= 1: no borrow
+        bad |= par;
+    }
+    return bad;
+}
+
 // int8 syndrome: bit 7 of byte b set when frame b has an unsatisfied check.
-template <int DMAX>
+template <int DS>
 __device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint32_t *Zs,
                                                     int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
-        for (int t = 0; t < c.rpl; ++t) {
-            if (lane + 32 * t >= c.z) break;
-            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
-            uint32_t off[DMAX];
-#pragma unroll
-            for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
-            // bit 7 of (u - 1) is set iff Z >= 1, so each of the DMAX terms (the
-            // dummy +127 ones included) flips the parity of the hard decisions
-            uint32_t par = (DMAX & 1) ? 0x80808080u : 0u;
-#pragma unroll
-            for (int i = 0; i < DMAX; ++i)
-                par ^= lds_u32(Zs, off[i]) - 0x01010101u;   // bytes >= 1: no borrow
-            bad |= par;
-        }
+        const int d = __ldg(c.rowinfo + l) & 255;
+        bad |= use_sub_i8<DS>(d) ? syndrome_rows_i8<DS, sub_slots<DS>()>(c, Zs, l, lane)
+                                 : syndrome_rows_i8<DS, DS>(c, Zs, l, lane);
     }
     return __reduce_or_sync(kFull, bad & 0x80808080u);
+}
+
+// One int8 layer through the instance that fits it.
+template <int DS>
+__device__ __forceinline__ void layer_i8_any(const DevCode &c, int layer, uint32_t *Zs,
+                                             uint32_t *rows, int lane, bool norm) {
+    const int d = __ldg(c.rowinfo + layer) & 255;
+    if (use_sub_i8<DS>(d))
+        layer_i8<DS, sub_slots<DS>()>(c, layer, d, Zs, rows, lane, norm);
+    else
+        layer_i8<DS, DS>(c, layer, d, Zs, rows, lane, norm);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,8 +507,8 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
             __syncwarp();
         }
         for (int l = 0; l < c.mb; ++l) {
-            layer_f32<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
-                                wcur + l * WP);
+            layer_f32_any<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
+                                    wcur + l * WP);
             __syncwarp();
         }
         if (p.early_stop && syndrome_ok_f32<DMAX>(c, Zs, lane)) return k;

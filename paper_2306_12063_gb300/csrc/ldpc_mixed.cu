@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(32)
             for (int b = 0; b < 4; ++b) any |= fr[b] >= 0;
             if (!any) break;
             for (int l = 0; l < c.mb; ++l) {
-                layer_i8<DMAX>(c, l, Zs, rows, lane, norm);
+                layer_i8_any<DMAX>(c, l, Zs, rows, lane, norm);
                 __syncwarp();
             }
             const uint32_t bad = p.early_stop ? syndrome_bad_i8<DMAX>(c, Zs, lane) : 0x80808080u;
