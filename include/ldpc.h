@@ -393,6 +393,43 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
 ldpc_status ldpc_mixed_scatter(const ldpc_mixed_plan *plan, int code, int what,
                                const void *d_src, void *d_dst, cudaStream_t stream);
 
+/* Learned weights of a mixed batch: h_weights[c] (device pointer to
+ * float[T_c][nnz(H_bm of code c)], as for ldpc_decode_learned_minsum) and
+ * h_T[c] = T_c for every code c of the set (host arrays of the set's size;
+ * entries of codes without frames may be NULL / 0).  The pointers are copied;
+ * the weight arrays must stay valid while the plan decodes with them. */
+ldpc_status ldpc_mixed_set_weights(ldpc_mixed_plan *plan, const float *const *h_weights,
+                                   const int32_t *h_T);
+
+/* Learned normalised min-sum over a mixed batch: every frame decoded by the
+ * learned FP32 decoder of its code (at most T_c iterations, syndrome stop if
+ * early_stop) in the plan's launches.  d_llr float (plan layout); d_hard,
+ * d_iters, d_post (NULL or float at llr_off) in the plan layout. */
+ldpc_status ldpc_decode_mixed_learned(ldpc_mixed_plan *plan, const float *d_llr, int early_stop,
+                                      uint32_t *d_hard, int32_t *d_iters, float *d_post,
+                                      cudaStream_t stream);
+
+/* d_bad uint8[frames]: 1 where a frame's hard decisions (plan layout)
+ * violate a parity check (eq. 21 termination test), else 0. */
+ldpc_status ldpc_mixed_frame_flags(const ldpc_mixed_plan *plan, const uint32_t *d_hard,
+                                   uint8_t *d_bad, cudaStream_t stream);
+
+/* Moves frames between two plans of the same code set, where frame s of
+ * plan B is frame d_index[s] (int64, device) of plan A: what = 0 copies LLR
+ * rows A -> B (float, plan layouts), 1 copies hard-decision rows B -> A,
+ * 2 writes iteration counts B -> A adding T_c of plan A's weights (the
+ * fallback's count after T_c learned iterations). */
+ldpc_status ldpc_mixed_move_frames(const ldpc_mixed_plan *plan_a, const ldpc_mixed_plan *plan_b,
+                                   const int64_t *d_index, int what, void *d_a, void *d_b,
+                                   cudaStream_t stream);
+
+/* Paired outcomes of two decoders over a mixed batch (as
+ * ldpc_paired_frame_errors): d_counts int64[4] = both right, only B wrong,
+ * only A wrong, both wrong. */
+ldpc_status ldpc_mixed_paired_errors(const ldpc_mixed_plan *plan, const uint8_t *d_info,
+                                     const uint32_t *d_hard_a, const uint32_t *d_hard_b,
+                                     int64_t *d_counts, cudaStream_t stream);
+
 /* A CUDA graph of one whole step on fixed buffers: [LDPC_I8X4: quantise
  * d_llr into d_q] -> the decode launches of every group (parallel branches)
  * -> [if d_counters: ldpc_mixed_stats against d_info with max_iters =

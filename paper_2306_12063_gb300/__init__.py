@@ -112,6 +112,11 @@ def load(build_if_missing: bool = False):
         "ldpc_quantize_i16": ([vp, vp, i64, f32, i32, vp], i32),
         "ldpc_encode_bitmap": ([vp, vp, vp, i64, vp], i32),
         "ldpc_decode_flooding_minsum": ([vp, vp, i64, P(_Params), vp, vp, vp, vp], i32),
+        "ldpc_mixed_set_weights": ([vp, vp, vp], i32),
+        "ldpc_decode_mixed_learned": ([vp, vp, i32, vp, vp, vp, vp], i32),
+        "ldpc_mixed_frame_flags": ([vp, vp, vp, vp], i32),
+        "ldpc_mixed_move_frames": ([vp, vp, vp, i32, vp, vp, vp], i32),
+        "ldpc_mixed_paired_errors": ([vp, vp, vp, vp, vp, vp], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -493,6 +498,50 @@ class MixedPlan:
         _check(load().ldpc_mixed_autotune(self._h, int(dtype), _ptr(d_in), ctypes.byref(p),
                                           _ptr(hard), _ptr(iters), int(reps), _stream(stream)))
         return self.groups()
+
+    def set_weights(self, weights):
+        """weights: per code of the set, a float32 [T][nnz_blocks] device tensor
+        (or None for codes without frames)."""
+        n = len(self.codeset)
+        ptrs = (ctypes.c_void_p * n)(*[(_ptr(w) if w is not None else None) for w in weights])
+        T = np.array([(w.shape[0] if w is not None else 0) for w in weights], dtype=np.int32)
+        self._weights = list(weights)
+        self.T = T
+        _check(load().ldpc_mixed_set_weights(self._h, ptrs, T.ctypes.data_as(ctypes.c_void_p)))
+
+    def decode_learned(self, llr, early_stop: bool = True, want_post: bool = False, out=None,
+                       stream=None):
+        torch = _torch()
+        if out is None:
+            hard, iters = self.empty_outputs()
+            post = (torch.empty((self.llr_elems,), dtype=torch.float32, device=llr.device)
+                    if want_post else None)
+        else:
+            hard, iters, post = out
+        _check(load().ldpc_decode_mixed_learned(self._h, _ptr(llr), int(bool(early_stop)),
+                                                _ptr(hard), _ptr(iters), _ptr(post),
+                                                _stream(stream)))
+        return hard, iters, post
+
+    def frame_flags(self, hard, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.frames,), dtype=torch.uint8, device=hard.device)
+        _check(load().ldpc_mixed_frame_flags(self._h, _ptr(hard), _ptr(out), _stream(stream)))
+        return out
+
+    def move_frames(self, sub, d_index, what: int, a, b, stream=None):
+        """Frame s of plan `sub` is frame d_index[s] of this plan (see
+        ldpc_mixed_move_frames for `what`)."""
+        _check(load().ldpc_mixed_move_frames(self._h, sub._h, _ptr(d_index), int(what), _ptr(a),
+                                             _ptr(b), _stream(stream)))
+
+    def paired_errors(self, info, hard_a, hard_b, stream=None):
+        torch = _torch()
+        out = torch.empty((4,), dtype=torch.int64, device=hard_a.device)
+        _check(load().ldpc_mixed_paired_errors(self._h, _ptr(info), _ptr(hard_a), _ptr(hard_b),
+                                               _ptr(out), _stream(stream)))
+        return out
 
     def scatter(self, code_index: int, what: int, src, dst, stream=None):
         _check(load().ldpc_mixed_scatter(self._h, int(code_index), int(what), _ptr(src),

@@ -522,11 +522,8 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
 // whether the hard decisions satisfy every check (eq. 21 termination test),
 // both warp-uniform.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long frame_outcome(const DevCode &c, const uint8_t *in,
-                                                            const uint32_t *h, int lane,
-                                                            bool *syn_ok) {
-    unsigned long long errs = 0;
-    for (int t = lane; t < c.k; t += 32) errs += ((h[t >> 5] >> (t & 31)) & 1u) ^ (in[t] & 1u);
+// True (warp-uniform) when the packed hard decisions h satisfy every check.
+__device__ __forceinline__ bool hard_syndrome_ok(const DevCode &c, const uint32_t *h, int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
         const int d = c.rowinfo[l] & 255;
@@ -541,8 +538,16 @@ __device__ __forceinline__ unsigned long long frame_outcome(const DevCode &c, co
             bad |= par;
         }
     }
+    return !__any_sync(kFull, bad);
+}
+
+__device__ __forceinline__ unsigned long long frame_outcome(const DevCode &c, const uint8_t *in,
+                                                            const uint32_t *h, int lane,
+                                                            bool *syn_ok) {
+    unsigned long long errs = 0;
+    for (int t = lane; t < c.k; t += 32) errs += ((h[t >> 5] >> (t & 31)) & 1u) ^ (in[t] & 1u);
     for (int o = 16; o; o >>= 1) errs += __shfl_xor_sync(kFull, errs, o);
-    *syn_ok = !__any_sync(kFull, bad);
+    *syn_ok = hard_syndrome_ok(c, h, lane);
     return errs;
 }
 

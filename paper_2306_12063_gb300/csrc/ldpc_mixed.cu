@@ -36,14 +36,17 @@ struct MixedItem {
 namespace {
 
 // One FP32 launch: work items of the group's codes, one frame at a time.
-template <int DMAX>
+// WT: learned normalised min-sum with code c's weights wptr[c] and
+// iteration count wT[c] (staged per iteration after the row state).
+template <int DMAX, bool WT = false>
 __global__ void __launch_bounds__(32)
     mixed_f32_kernel(const DevCode *__restrict__ codes, const MixedItem *__restrict__ items,
                      int n_items, const long long *__restrict__ uframe,
                      const long long *__restrict__ llr_off, const long long *__restrict__ hard_off,
                      const float *__restrict__ llr, DecodeParams p, uint32_t *__restrict__ hard,
                      int32_t *__restrict__ iters, float *__restrict__ post,
-                     unsigned long long *work, int use_bulk) {
+                     unsigned long long *work, int use_bulk, const float *const *wptr,
+                     const int *wT) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -59,15 +62,22 @@ __global__ void __launch_bounds__(32)
         const MixedItem item = items[it];
         const DevCode c = codes[item.code];
         uint32_t *rows = Zs + ((c.n + 4) & ~3);
+        float *wbuf = reinterpret_cast<float *>(rows + ((c.m * 3 + 3) & ~3));
+        DecodeParams pc = p;
+        if (WT) {
+            pc.weights = wptr[item.code];
+            pc.max_iters = wT[item.code];
+            pc.n_edges = c.n_edges;
+        }
         if (lane == 0) Zs[c.n] = 0x7F800000u;   // dummy posterior of unused edge slots
         __syncwarp();
         for (long long i = item.start; i < item.start + item.count; ++i) {
             const long long uf = uframe[i];
             if (uf < 0) continue;   // padding of the code's range
             const float *src = llr + llr_off[uf];
-            const int done = decode_one_f32<DMAX, false>(
-                c, Zs, rows, nullptr, reinterpret_cast<const uint32_t *>(src), use_bulk != 0,
-                bar, phase, p, lane);
+            const int done = decode_one_f32<DMAX, WT>(
+                c, Zs, rows, wbuf, reinterpret_cast<const uint32_t *>(src), use_bulk != 0,
+                bar, phase, pc, lane);
             if (!done) return;
             write_frame_f32_to(c, Zs, done, hard + hard_off[uf], iters + uf,
                                post ? post + llr_off[uf] : nullptr, lane);
@@ -249,6 +259,79 @@ __global__ void mixed_stats_kernel(const DevCode *__restrict__ codes,
     }
 }
 
+// 1 for every frame whose hard decisions violate a check (warp per frame).
+__global__ void mixed_flags_kernel(const DevCode *__restrict__ codes,
+                                   const int *__restrict__ code_of_frame, long long frames,
+                                   const long long *__restrict__ hard_off,
+                                   const uint32_t *__restrict__ hard, uint8_t *__restrict__ bad) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+    for (long long f = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+         f < frames; f += warps) {
+        const DevCode c = codes[code_of_frame[f]];
+        const bool ok = hard_syndrome_ok(c, hard + hard_off[f], lane);
+        if (lane == 0) bad[f] = ok ? 0 : 1;
+    }
+}
+
+// Frame s of plan B is frame idx[s] of plan A (same code set).  what = 0:
+// LLR row A -> B; 1: hard-decision row B -> A; 2: iteration count B -> A plus
+// add[code].  Block per frame of B.
+__global__ void mixed_move_kernel(const DevCode *__restrict__ codes,
+                                  const int *__restrict__ code_b, long long frames_b,
+                                  const long long *__restrict__ idx,
+                                  const long long *__restrict__ off_a,
+                                  const long long *__restrict__ off_b, int what,
+                                  uint32_t *__restrict__ a, uint32_t *__restrict__ b,
+                                  const int *__restrict__ add) {
+    for (long long s = blockIdx.x; s < frames_b; s += gridDim.x) {
+        const long long fa = idx[s];
+        const int ci = code_b[s];
+        if (what == 2) {
+            if (threadIdx.x == 0)
+                a[fa] = static_cast<uint32_t>(static_cast<int>(b[s]) + (add ? add[ci] : 0));
+            continue;
+        }
+        const int n = what == 0 ? codes[ci].n : codes[ci].nwords;
+        uint32_t *pa = a + off_a[fa];
+        uint32_t *pb = b + off_b[s];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            if (what == 0)
+                pb[i] = pa[i];
+            else
+                pa[i] = pb[i];
+        }
+    }
+}
+
+// Paired outcomes of two decoders over a mixed batch (as
+// ldpc_paired_frame_errors): cnt[2 a + b], a / b = decoder A / B wrong.
+__global__ void mixed_paired_kernel(const DevCode *__restrict__ codes,
+                                    const int *__restrict__ code_of_frame, long long frames,
+                                    const long long *__restrict__ info_off,
+                                    const long long *__restrict__ hard_off,
+                                    const uint8_t *__restrict__ info,
+                                    const uint32_t *__restrict__ ha,
+                                    const uint32_t *__restrict__ hb,
+                                    unsigned long long *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+    for (long long f = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+         f < frames; f += warps) {
+        const int k = codes[code_of_frame[f]].k;
+        const uint8_t *in = info + info_off[f];
+        const uint32_t *pa = ha + hard_off[f], *pb = hb + hard_off[f];
+        uint32_t ea = 0, eb = 0;
+        for (int t = lane; t < k; t += 32) {
+            const uint32_t x = in[t] & 1u;
+            ea |= ((pa[t >> 5] >> (t & 31)) & 1u) ^ x;
+            eb |= ((pb[t >> 5] >> (t & 31)) & 1u) ^ x;
+        }
+        const bool wa = __any_sync(0xFFFFFFFFu, ea), wb = __any_sync(0xFFFFFFFFu, eb);
+        if (lane == 0) atomicAdd(&cnt[2 * (wa ? 1 : 0) + (wb ? 1 : 0)], 1ull);
+    }
+}
+
 // Rows of one code's frames (consecutive in src, the code's frames in batch
 // order) copied to their places in the plan layout: block per frame.
 __global__ void mixed_scatter_kernel(const long long *__restrict__ uframe, long long first,
@@ -279,6 +362,7 @@ struct MixedGroup {
     int dslots = 0;
     std::vector<int> codes;              // set indices, largest first
     int smem[2] = {0, 0};                // bytes per block: [0] FP32, [1] int8
+    int smem_learned = 0;                // FP32 plus two iterations of staged weights
     int chunk[2] = {8, 16};              // frames per work item
     int per_sm[2] = {0, 0};              // resident blocks per SM (0: occupancy limit)
     MixedItem *d_items[2] = {nullptr, nullptr};
@@ -306,6 +390,10 @@ struct MixedPlan {
     unsigned long long *d_work = nullptr;                // one counter per group and dtype
     std::vector<MixedGroup> groups;     // heaviest (edges x frames) first
     bool serial[2] = {false, false};     // groups one after another on the caller's stream
+    // learned weights per set code (device pointers) and their iteration counts
+    const float **d_wptr = nullptr;
+    int *d_wT = nullptr;
+    std::vector<int> wT;
     cudaEvent_t fork = nullptr;
     std::mutex mu;                                       // item rebuilds
 };
@@ -371,18 +459,24 @@ static void release_plan(MixedPlan *pl) {
     cudaFree(pl->d_group_first);
     cudaFree(pl->d_group_qoff);
     cudaFree(pl->d_work);
+    cudaFree(pl->d_wptr);
+    cudaFree(pl->d_wT);
     if (pl->fork) cudaEventDestroy(pl->fork);
     cudaSetDevice(prev);
     delete pl;
 }
 
+// dt: 0 FP32, 1 int8, 2 FP32 learned (FP32 work items and counter).
 template <int DMAX>
 static ldpc_status launch_group_t(MixedPlan &pl, MixedGroup &g, int gi, int dt, const void *d_in,
                                   const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                   void *d_post, cudaStream_t s) {
-    const int smem = g.smem[dt];
-    const void *kern = dt == 0 ? reinterpret_cast<const void *>(mixed_f32_kernel<DMAX>)
-                               : reinterpret_cast<const void *>(mixed_i8_kernel<DMAX>);
+    const bool learned = dt == 2;
+    if (learned) dt = 0;
+    const int smem = learned ? g.smem_learned : g.smem[dt];
+    const void *kern = dt == 1 ? reinterpret_cast<const void *>(mixed_i8_kernel<DMAX>)
+                       : learned ? reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, true>)
+                                 : reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "mixed kernel attribute");
     int per_sm = 0, sms = 148;
@@ -392,16 +486,22 @@ static ldpc_status launch_group_t(MixedPlan &pl, MixedGroup &g, int gi, int dt, 
     per_sm = std::max(per_sm, 1);
     if (g.per_sm[dt] > 0) per_sm = std::min(per_sm, g.per_sm[dt]);
     const int grid = std::max(1, std::min(g.n_items[dt], per_sm * sms));
-    unsigned long long *work = pl.d_work + 2 * gi + dt;
+    unsigned long long *work = pl.d_work + 2 * gi + (dt == 1 ? 1 : 0);
     e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed work counter");
     const DevCode *codes = pl.set->d_desc;
     if (dt == 0) {
         const bool bulk = g.bulk_ok && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
-        mixed_f32_kernel<DMAX><<<grid, 32, smem, s>>>(
-            codes, g.d_items[0], g.n_items[0], pl.d_uframe, pl.d_llr_off, pl.d_hard_off,
-            static_cast<const float *>(d_in), p, d_hard, d_iters, static_cast<float *>(d_post),
-            work, bulk ? 1 : 0);
+        if (learned)
+            mixed_f32_kernel<DMAX, true><<<grid, 32, smem, s>>>(
+                codes, g.d_items[0], g.n_items[0], pl.d_uframe, pl.d_llr_off, pl.d_hard_off,
+                static_cast<const float *>(d_in), p, d_hard, d_iters,
+                static_cast<float *>(d_post), work, bulk ? 1 : 0, pl.d_wptr, pl.d_wT);
+        else
+            mixed_f32_kernel<DMAX, false><<<grid, 32, smem, s>>>(
+                codes, g.d_items[0], g.n_items[0], pl.d_uframe, pl.d_llr_off, pl.d_hard_off,
+                static_cast<const float *>(d_in), p, d_hard, d_iters,
+                static_cast<float *>(d_post), work, bulk ? 1 : 0, nullptr, nullptr);
     } else {
         const bool bulk = g.bulk_ok && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
         mixed_i8_kernel<DMAX><<<grid, 32, smem, s>>>(
@@ -417,14 +517,15 @@ static ldpc_status launch_group(MixedPlan &pl, int gi, int dt, const void *d_in,
                                 const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                 void *d_post, cudaStream_t s) {
     MixedGroup &g = pl.groups[gi];
-    if (g.built_chunk[dt] != g.chunk[dt]) {
+    const int it = dt == 2 ? 0 : dt;   // the learned decoder uses the FP32 work items
+    if (g.built_chunk[it] != g.chunk[it]) {
         std::lock_guard<std::mutex> lock(pl.mu);
-        if (g.built_chunk[dt] != g.chunk[dt]) {
-            ldpc_status st = build_items(pl, g, dt, g.chunk[dt]);
+        if (g.built_chunk[it] != g.chunk[it]) {
+            ldpc_status st = build_items(pl, g, it, g.chunk[it]);
             if (st != LDPC_OK) return st;
         }
     }
-    if (g.n_items[dt] == 0) return LDPC_OK;
+    if (g.n_items[it] == 0) return LDPC_OK;
     switch (g.dslots) {
 #define LDPC_MIXED_CASE(D) \
     case D: return launch_group_t<D>(pl, g, gi, dt, d_in, p, d_hard, d_iters, d_post, s);
@@ -438,7 +539,7 @@ static ldpc_status launch_group(MixedPlan &pl, int gi, int dt, const void *d_in,
 // when the plan says so, one after another on `s`).
 static ldpc_status launch_all(MixedPlan &pl, int dt, const void *d_in, const DecodeParams &p,
                               uint32_t *d_hard, int32_t *d_iters, void *d_post, cudaStream_t s) {
-    if (pl.serial[dt]) {
+    if (pl.serial[dt == 1 ? 1 : 0]) {
         for (size_t gi = 0; gi < pl.groups.size(); ++gi) {
             ldpc_status st = launch_group(pl, static_cast<int>(gi), dt, d_in, p, d_hard, d_iters,
                                           d_post, s);
@@ -604,6 +705,8 @@ ldpc_status ldpc_mixed_plan_create(const ldpc_codeset *set, const int32_t *h_cod
         MixedGroup &g = pl->groups.back();
         g.codes.push_back(ci);
         g.smem[0] = std::max(g.smem[0], region_bytes_f32(c));
+        g.smem_learned = std::max(g.smem_learned,
+                                  region_bytes_f32(c) + 8 * c.mb * ((c.dslots + 3) & ~3));
         g.smem[1] = std::max(g.smem[1], si8);
         if (c.n % 4) g.bulk_ok = false;
         if (!all_n4) g.bulk_ok = false;
@@ -1007,6 +1110,125 @@ void ldpc_mixed_graph_destroy(ldpc_mixed_graph *graph) {
     if (graph->cap) cudaStreamDestroy(graph->cap);
     cudaSetDevice(prev);
     delete graph;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+ldpc_status ldpc_mixed_set_weights(ldpc_mixed_plan *plan, const float *const *h_weights,
+                                   const int32_t *h_T) {
+    if (!plan || !h_weights || !h_T)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_set_weights: NULL argument");
+    MixedPlan &p = *plan->p;
+    const int count = static_cast<int>(p.set->codes.size());
+    for (int ci = 0; ci < count; ++ci) {
+        if (!p.fcount[ci]) continue;
+        if (!h_weights[ci] || h_T[ci] < 1 || h_T[ci] > kMaxIters)
+            return fail(LDPC_ERR_INVALID_ARG,
+                        "ldpc_mixed_set_weights: code " + std::to_string(ci) +
+                            " has frames but no weights or T outside 1..1000");
+    }
+    ldpc_status st = bind_plan(p);
+    if (st != LDPC_OK) return st;
+    std::vector<const float *> w(h_weights, h_weights + count);
+    std::vector<int> T(h_T, h_T + count);
+    cudaFree(p.d_wptr);
+    cudaFree(p.d_wT);
+    p.d_wptr = nullptr;
+    p.d_wT = nullptr;
+    cudaError_t e = upload(&p.d_wptr, w);
+    if (e == cudaSuccess) e = upload(&p.d_wT, T);
+    if (e != cudaSuccess) return cuda_fail(e, "ldpc_mixed_set_weights");
+    p.wT = T;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_decode_mixed_learned(ldpc_mixed_plan *plan, const float *d_llr, int early_stop,
+                                      uint32_t *d_hard, int32_t *d_iters, float *d_post,
+                                      cudaStream_t stream) {
+    if (!plan) return fail(LDPC_ERR_INVALID_ARG, "ldpc_decode_mixed_learned: plan is NULL");
+    if (early_stop != 0 && early_stop != 1)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_decode_mixed_learned: early_stop must be 0 or 1");
+    MixedPlan &p = *plan->p;
+    if (p.frames == 0) return LDPC_OK;
+    if (!p.d_wptr)
+        return fail(LDPC_ERR_INVALID_ARG,
+                    "ldpc_decode_mixed_learned: no weights (ldpc_mixed_set_weights)");
+    if (!d_llr || !d_hard || !d_iters)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_decode_mixed_learned: NULL buffer");
+    ldpc_status st = bind_plan(p);
+    if (st != LDPC_OK) return st;
+    DecodeParams dp;
+    dp.max_iters = 1;   // per code from the weight table
+    dp.alpha = 1.0f;
+    dp.normalise = 0;
+    dp.early_stop = early_stop;
+    return launch_all(p, 2, d_llr, dp, d_hard, d_iters, d_post, stream);
+}
+
+ldpc_status ldpc_mixed_frame_flags(const ldpc_mixed_plan *plan, const uint32_t *d_hard,
+                                   uint8_t *d_bad, cudaStream_t stream) {
+    if (!plan) return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_frame_flags: plan is NULL");
+    const MixedPlan &p = *plan->p;
+    if (p.frames == 0) return LDPC_OK;
+    if (!d_hard || !d_bad) return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_frame_flags: NULL buffer");
+    ldpc_status st = bind_plan(p);
+    if (st != LDPC_OK) return st;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+    const long long grid = std::min<long long>((p.frames + 7) / 8, 32LL * sms);
+    mixed_flags_kernel<<<static_cast<unsigned>(grid), 256, 0, stream>>>(
+        p.set->d_desc, p.d_code_of_frame, p.frames, p.d_hard_off, d_hard, d_bad);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "mixed_flags_kernel");
+}
+
+ldpc_status ldpc_mixed_move_frames(const ldpc_mixed_plan *plan_a, const ldpc_mixed_plan *plan_b,
+                                   const int64_t *d_index, int what, void *d_a, void *d_b,
+                                   cudaStream_t stream) {
+    if (!plan_a || !plan_b || what < 0 || what > 2)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_move_frames: bad plans or kind");
+    const MixedPlan &a = *plan_a->p, &b = *plan_b->p;
+    if (a.set != b.set)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_move_frames: plans of different code sets");
+    if (b.frames == 0) return LDPC_OK;
+    if (!d_index || !d_a || !d_b)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_move_frames: NULL buffer");
+    ldpc_status st = bind_plan(a);
+    if (st != LDPC_OK) return st;
+    const long long *off_a = what == 0 ? a.d_llr_off : a.d_hard_off;
+    const long long *off_b = what == 0 ? b.d_llr_off : b.d_hard_off;
+    const unsigned grid = static_cast<unsigned>(std::min<long long>(b.frames, 65535));
+    mixed_move_kernel<<<grid, 128, 0, stream>>>(
+        a.set->d_desc, b.d_code_of_frame, b.frames, reinterpret_cast<const long long *>(d_index),
+        off_a, off_b, what, static_cast<uint32_t *>(d_a), static_cast<uint32_t *>(d_b),
+        what == 2 ? a.d_wT : nullptr);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "mixed_move_kernel");
+}
+
+ldpc_status ldpc_mixed_paired_errors(const ldpc_mixed_plan *plan, const uint8_t *d_info,
+                                     const uint32_t *d_hard_a, const uint32_t *d_hard_b,
+                                     int64_t *d_counts, cudaStream_t stream) {
+    if (!plan || !d_counts)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_paired_errors: NULL plan or counts");
+    const MixedPlan &p = *plan->p;
+    ldpc_status st = bind_plan(p);
+    if (st != LDPC_OK) return st;
+    cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(int64_t) * 4, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
+    if (p.frames == 0) return LDPC_OK;
+    if (!d_info || !d_hard_a || !d_hard_b)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_paired_errors: NULL buffer");
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+    const long long grid = std::min<long long>((p.frames + 7) / 8, 32LL * sms);
+    mixed_paired_kernel<<<static_cast<unsigned>(grid), 256, 0, stream>>>(
+        p.set->d_desc, p.d_code_of_frame, p.frames, p.d_info_off, p.d_hard_off, d_info, d_hard_a,
+        d_hard_b, reinterpret_cast<unsigned long long *>(d_counts));
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "mixed_paired_kernel");
 }
 
 }  // extern "C"

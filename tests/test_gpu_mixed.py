@@ -140,3 +140,61 @@ def test_mixed_stats_and_graph(ldpc):
         torch.cuda.synchronize()
         assert torch.equal(h2, hard) and torch.equal(i2, iters)
         assert torch.equal(c2, cnt) and torch.equal(f2, fe) and torch.equal(q2, q)
+
+
+def test_mixed_learned_and_fallback(ldpc):
+    """Learned decoding over a mixed batch (per-code weights, per-code T)
+    equals the oracle's weighted decoder frame by frame; the fallback
+    pipeline equals the oracle's two steps (learned, then int8 plain min-sum
+    at 20 iterations on the frames whose syndrome is not zero)."""
+    from paper_2306_12063_gb300.mixed_learned import decode_learned_fallback
+    shapes = _shapes()
+    codes, cs, plan, batch = _setup(ldpc, shapes, 600, seed=12, ebn0=(1.0, 3.5))
+    rng = np.random.default_rng(2)
+    Ts = [int(rng.integers(3, 9)) for _ in shapes]
+    ws = [rng.uniform(0.5, 1.0, (T, c.nnz_blocks)).astype(np.float32) for T, c in zip(Ts, codes)]
+    plan.set_weights([torch.from_numpy(w).cuda() for w in ws])
+    hard, iters, post = plan.decode_learned(batch.llr, early_stop=True, want_post=True)
+    fb_hard, fb_iters, nfb = decode_learned_fallback(plan, batch.llr)
+    llr_h = batch.llr.cpu().numpy()
+    hw, it, pw = hard.cpu().numpy().view(np.uint32), iters.cpu().numpy(), post.cpu().numpy()
+    fhw, fit = fb_hard.cpu().numpy().view(np.uint32), fb_iters.cpu().numpy()
+    bad_total = 0
+    for ci, s in enumerate(shapes):
+        idx = np.nonzero(plan.code_of_frame == ci)[0]
+        if idx.size == 0:
+            continue
+        rc = oracle.RefCode(s.hbm, s.z)
+        x = np.stack([llr_h[plan.llr_off[f]:plan.llr_off[f] + rc.n] for f in idx])
+        h, i, p = rc.decode_layered_weighted_f32(x, ws[ci], Ts[ci], early_stop=True)
+        bits = oracle.unpack_hard(h, rc.n)
+        bad = np.array([rc.syndrome_weight(b) != 0 for b in bits])
+        bad_total += int(bad.sum())
+        hq = h.copy()
+        iq = i.copy()
+        if bad.any():
+            h8, i8, _, _ = rc.decode_layered_i8(oracle.quantize_i8(x[bad]), 20, True, True,
+                                                want_post=False)
+            hq[bad] = h8
+            iq[bad] = Ts[ci] + i8
+        for j, f in enumerate(idx):
+            a, b = plan.hard_off[f], plan.hard_off[f + 1]
+            assert it[f] == i[j] and (hw[a:b] == h[j]).all()
+            assert (pw[plan.llr_off[f]:plan.llr_off[f + 1]] == p[j]).all()
+            assert fit[f] == iq[j] and (fhw[a:b] == hq[j]).all()
+    assert nfb == bad_total and 0 < nfb < plan.frames
+    # per-frame flags and paired outcomes against host counts
+    flags = plan.frame_flags(hard).cpu().numpy()
+    assert flags.sum() == bad_total
+    cnt = plan.paired_errors(batch.info, hard, fb_hard).cpu().numpy()
+    info = batch.info.cpu().numpy()
+    wa = np.zeros(plan.frames, bool)
+    wb = np.zeros(plan.frames, bool)
+    for f in range(plan.frames):
+        c = codes[plan.code_of_frame[f]]
+        a, b = plan.hard_off[f], plan.hard_off[f + 1]
+        ref = info[plan.info_off[f]:plan.info_off[f + 1]]
+        wa[f] = (oracle.unpack_hard(hw[a:b][None], c.n)[0][:c.k] != ref).any()
+        wb[f] = (oracle.unpack_hard(fhw[a:b][None], c.n)[0][:c.k] != ref).any()
+    assert cnt.tolist() == [int((~wa & ~wb).sum()), int((~wa & wb).sum()),
+                            int((wa & ~wb).sum()), int((wa & wb).sum())]
