@@ -377,6 +377,160 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     return res
 
 
+SCALE_WORKLOAD = ("learned vs plain at scale: the 76 WiMAX-shaped codes plus the N=648 and "
+                  "N=1944 Wi-Fi-shaped codes, frames interleaved at random over the 78 codes "
+                  "(seed 3), Eb/N0 uniform in [1.5, 4.5) dB per frame")
+
+
+def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
+    """Learned normalised min-sum (per-code weights, T = 8 up to rate 2/3 and
+    6 above) with its int8 plain fallback against plain min-sum at 20
+    iterations on the same mixed batch, plus the oracle's FER of the learned
+    pipeline on a subset of the frames."""
+    from paper_2306_12063_gb300 import stats, train
+    from paper_2306_12063_gb300.mixed_learned import decode_learned_fallback
+    from paper_2306_12063_gb300.shard import reduce_counters
+    from paper_2306_12063_gb300.workload import make_mixed_batch, mixed_frame_id
+
+    shapes = synth.wimax_mixed_set() + [synth.wifi_n648_r12(), synth.wifi_n1944_r56()]
+    codes = [ldpc.Code(s.hbm, s.z, device=dev) for s in shapes]
+    cs = ldpc.CodeSet(codes)
+    F = args.scale_frames
+    cof, _ = synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)
+    cof = np.ascontiguousarray(cof[rank * F:(rank + 1) * F])
+    plan = ldpc.MixedPlan(cs, cof)
+    batch = make_mixed_batch(plan, LEARNED_EBN0, seed=1)
+    counts = np.bincount(cof, minlength=len(shapes))
+    # per-code training on the library's own generators (bounded budget)
+    t0 = time.time()
+    weights = []
+    for ci, code in enumerate(codes):
+        if counts[ci] == 0:
+            weights.append(None)
+            continue
+        T = train.default_iterations(code.k / code.n)
+        cfg = train.TrainConfig(T=T, steps=args.scale_train_steps, batch=1024, lr=2e-3,
+                                seed=1000 + ci)
+        weights.append(train.train_weights(code, cfg).weights)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    plan.set_weights(weights)
+    q = plan.quantize(batch.llr)
+    outs = {k: plan.empty_outputs() for k in ("plain_i8_20", "plain_f32_20", "learned",
+                                               "learned_fallback")}
+    plan.autotune(q, ldpc.I8X4, max_iters=MAX_ITERS, reps=2, out=outs["plain_i8_20"])
+    plan.autotune(batch.llr, ldpc.F32, max_iters=MAX_ITERS, reps=2, out=outs["plain_f32_20"])
+    fbn = [0]
+
+    def run(name):
+        o = outs[name]
+        if name == "plain_i8_20":
+            plan.decode(q, ldpc.I8X4, max_iters=MAX_ITERS, out=(o[0], o[1], None))
+        elif name == "plain_f32_20":
+            plan.decode(batch.llr, ldpc.F32, max_iters=MAX_ITERS, out=(o[0], o[1], None))
+        elif name == "learned":
+            plan.decode_learned(batch.llr, early_stop=True, out=(o[0], o[1], None))
+        else:
+            _, _, fbn[0] = decode_learned_fallback(plan, batch.llr, MAX_ITERS, out=o)
+
+    steps = max(1, args.steps // 4)
+    res = {}
+    info_bits = plan.info_elems * ws
+    for name in outs:
+        for _ in range(2):
+            run(name)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            run(name)
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = a.elapsed_time(b) / steps
+        if pg is not None:
+            tt = torch.tensor([ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            ms = float(tt.item())
+        mi = 28 if name == "learned_fallback" else MAX_ITERS
+        cnt, _ = plan.stats(batch.info, outs[name][0], outs[name][1], mi, per_code=False)
+        st = reduce_counters(cnt.cpu().numpy())
+        nf = F * ws
+        res[name] = {"value": info_bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms": ms,
+                     "fer": float(st[1]) / nf, "wilson95": stats.wilson_interval(int(st[1]), nf),
+                     "mean_iters": float(st[3]) / nf}
+    res["learned_fallback"]["fallback_frames"] = int(
+        reduce_counters(np.array([fbn[0]], dtype=np.int64))[0])
+    comps = {}
+    for plain in ("plain_i8_20", "plain_f32_20"):
+        for lrn in ("learned", "learned_fallback"):
+            cnt = reduce_counters(plan.paired_errors(batch.info, outs[lrn][0],
+                                                     outs[plain][0]).cpu().numpy())
+            c = stats.compare(cnt, F * ws)
+            c["speedup"] = res[lrn]["value"] / res[plain]["value"]
+            comps[f"{lrn}_vs_{plain}"] = c
+    out = {"workload": SCALE_WORKLOAD, "frames": F * ws, "codes": len(shapes),
+           "decoders": res, "comparisons": comps,
+           "training": {"per_code": {"steps": args.scale_train_steps, "batch": 1024, "lr": 2e-3,
+                                     "ebn0_db": [1.0, 4.0], "T": "8 (R <= 2/3), 6 (R > 2/3)"},
+                        "codes_trained": int((counts > 0).sum()), "seconds": train_s}}
+    # the oracle's FER of the learned pipeline on a subset (rank 0)
+    if rank == 0 and args.scale_oracle_frames > 0:
+        out["oracle_subset"] = _oracle_learned_subset(plan, shapes, weights, batch,
+                                                      outs["learned_fallback"],
+                                                      args.scale_oracle_frames)
+    return out
+
+
+def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub):
+    """The oracle's learned-then-int8-fallback decode of the first nsub frames
+    (thread pool over codes); FER against the GPU pipeline's on the same
+    frames (equal bit for bit)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    nsub = min(nsub, plan.frames)
+    llr = batch.llr[:int(plan.llr_off[nsub])].cpu().numpy()
+    info = batch.info[:int(plan.info_off[nsub])].cpu().numpy()
+    gpu_h = fb_out[0][:int(plan.hard_off[nsub])].cpu().numpy().view(np.uint32)
+    cof = plan.code_of_frame[:nsub]
+
+    def one(ci):
+        idx = np.nonzero(cof == ci)[0]
+        if idx.size == 0:
+            return 0, 0, 0
+        s = shapes[ci]
+        rc = oracle.RefCode(s.hbm, s.z)
+        w = weights[ci].cpu().numpy()
+        x = np.stack([llr[plan.llr_off[f]:plan.llr_off[f] + rc.n] for f in idx])
+        h, _, _ = rc.decode_layered_weighted_f32(x, w, w.shape[0], early_stop=True,
+                                                 want_post=False)
+        bits = oracle.unpack_hard(h, rc.n)
+        bad = np.array([rc.syndrome_weight(b) != 0 for b in bits])
+        if bad.any():
+            h8, _, _, _ = rc.decode_layered_i8(oracle.quantize_i8(x[bad]), MAX_ITERS, True,
+                                               True, want_post=False)
+            h = h.copy()
+            h[bad] = h8
+        bits = oracle.unpack_hard(h, rc.n)
+        fe = 0
+        same = 0
+        for j, f in enumerate(idx):
+            ref = info[plan.info_off[f]:plan.info_off[f + 1]]
+            fe += int((bits[j][:rc.k] != ref).any())
+            same += int((gpu_h[plan.hard_off[f]:plan.hard_off[f + 1]] == h[j]).all())
+        return idx.size, fe, same
+
+    t0 = time.time()
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        parts = list(ex.map(one, range(len(shapes))))
+    n = sum(p[0] for p in parts)
+    fe = sum(p[1] for p in parts)
+    same = sum(p[2] for p in parts)
+    return {"frames": n, "fer": fe / max(n, 1), "frames_equal_to_gpu": same,
+            "seconds": time.time() - t0}
+
+
 def variants_leg(args, ldpc, torch, dev, stream, barrier, code, batch, pg):
     """The paper's variants timed on the same inputs as the main decoders:
     Section 5's int16 wrap-around decoder and the flooding schedule on the
@@ -494,6 +648,10 @@ def main():
     ap.add_argument("--learned-frames", type=int, default=262144)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-scale", action="store_true")
+    ap.add_argument("--scale-frames", type=int, default=1048576)
+    ap.add_argument("--scale-train-steps", type=int, default=300)
+    ap.add_argument("--scale-oracle-frames", type=int, default=10000)
     ap.add_argument("--mixed-frames", type=int, default=65536)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -673,6 +831,9 @@ def main():
         res["learned"] = learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
     if not args.no_mixed:
         res["mixed"] = mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg)
+    if not args.no_scale:
+        res["learned_scale"] = learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank,
+                                                 ws, pg)
     if not args.no_variants and not args.no_fp32:
         res["variants"] = variants_leg(args, ldpc, torch, dev, stream, barrier, code, batches[1],
                                        pg)
