@@ -285,10 +285,11 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     codes = [ldpc.Code(s.hbm, s.z, device=dev) for s in shapes]
     cs = ldpc.CodeSet(codes)
     F = args.mixed_frames
-    cof, _ = synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)
-    cof = np.ascontiguousarray(cof[rank * F:(rank + 1) * F])
+    from paper_2306_12063_gb300.shard import mixed_shard
+    first, cof = mixed_shard(synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)[0], rank,
+                             ws)
     plan = ldpc.MixedPlan(cs, cof)
-    batch = make_mixed_batch(plan, LEARNED_EBN0, seed=1)
+    batch = make_mixed_batch(plan, LEARNED_EBN0, seed=1, frame_base=first)
     q = plan.quantize(batch.llr)
     hard, iters = plan.empty_outputs()
     info_bits = int(plan.info_elems)
@@ -322,7 +323,7 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     for ci, code in enumerate(codes):
         if counts[ci] == 0:
             continue
-        f0 = mixed_frame_id(ci, 0)
+        f0 = mixed_frame_id(ci, first)
         inf_c = ldpc.gen_info(1, f0, int(counts[ci]), code.k, device=dev)
         cw = code.encode(inf_c)
         sig = ldpc.snr_sigma(1, f0, int(counts[ci]), LEARNED_EBN0[0], LEARNED_EBN0[1],
@@ -396,10 +397,11 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     codes = [ldpc.Code(s.hbm, s.z, device=dev) for s in shapes]
     cs = ldpc.CodeSet(codes)
     F = args.scale_frames
-    cof, _ = synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)
-    cof = np.ascontiguousarray(cof[rank * F:(rank + 1) * F])
+    from paper_2306_12063_gb300.shard import mixed_shard
+    first, cof = mixed_shard(synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)[0], rank,
+                             ws)
     plan = ldpc.MixedPlan(cs, cof)
-    batch = make_mixed_batch(plan, LEARNED_EBN0, seed=1)
+    batch = make_mixed_batch(plan, LEARNED_EBN0, seed=1, frame_base=first)
     counts = np.bincount(cof, minlength=len(shapes))
     # per-code training on the library's own generators (bounded budget)
     t0 = time.time()

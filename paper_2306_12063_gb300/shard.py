@@ -26,6 +26,18 @@ def shard_range(total: int, rank: int, world: int) -> Tuple[int, int]:
     return start, base + (1 if rank < extra else 0)
 
 
+def mixed_shard(code_of_frame_all, rank: int, world: int):
+    """Rank's frames of a mixed batch under weak scaling: the global
+    assignment holds world * F frames (F per rank); rank r decodes frames
+    r F .. (r + 1) F - 1, keeping their codes and order.  Returns (first
+    global frame, the rank's code-of-frame array)."""
+    cof = np.asarray(code_of_frame_all)
+    if world < 1 or not 0 <= rank < world or cof.size % world:
+        raise ValueError("bad shard arguments")
+    per = cof.size // world
+    return rank * per, np.ascontiguousarray(cof[rank * per:(rank + 1) * per], dtype=np.int32)
+
+
 def reduce_counters(counters, op: str = "sum"):
     """All-reduce an int64 counter vector over the default process group
     (a no-op without one); returns a numpy array."""

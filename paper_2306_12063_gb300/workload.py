@@ -47,11 +47,14 @@ def mixed_frame_id(code_index: int, j: int) -> int:
     return (int(code_index) << 32) + int(j)
 
 
-def make_mixed_batch(plan, ebn0_db=(1.5, 4.5), seed: int = 1, stream=None) -> MixedBatch:
+def make_mixed_batch(plan, ebn0_db=(1.5, 4.5), seed: int = 1, frame_base: int = 0,
+                     stream=None) -> MixedBatch:
     """Every frame of the plan: info bits, direct encoding, Eb/N0 uniform in
     [lo, hi) dB per frame and the AWGN channel, generated per code by the
-    library's kernels (frame identities mixed_frame_id(c, j)) and placed in
-    the plan layout by ldpc_mixed_scatter."""
+    library's kernels and placed in the plan layout by ldpc_mixed_scatter.
+    The j-th frame of code c has identity mixed_frame_id(c, frame_base + j)
+    (ranks of a sharded batch pass their first global frame, so no two ranks
+    draw the same frame)."""
     import numpy as np
     import torch
     codes = plan.codeset.codes
@@ -63,7 +66,7 @@ def make_mixed_batch(plan, ebn0_db=(1.5, 4.5), seed: int = 1, stream=None) -> Mi
         F = int(counts[ci])
         if F == 0:
             continue
-        f0 = mixed_frame_id(ci, 0)
+        f0 = mixed_frame_id(ci, frame_base)
         inf_c = gen_info(seed, f0, F, code.k, device=dev, stream=stream)
         cw = code.encode(inf_c, stream=stream)
         sig = snr_sigma(seed, f0, F, ebn0_db[0], ebn0_db[1], code.k / code.n, device=dev,

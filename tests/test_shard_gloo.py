@@ -9,7 +9,8 @@ import pytest
 
 import oracle
 import synth
-from paper_2306_12063_gb300.shard import frame_offset, reduce_counters, shard_range
+from paper_2306_12063_gb300.shard import (frame_offset, mixed_shard, reduce_counters,
+                                          shard_range)
 
 FRAMES = 30
 EBN0 = 1.5
@@ -71,3 +72,60 @@ def test_two_gloo_ranks_match_one_process(tmp_path):
     want = _counters(0, FRAMES)
     assert got[:4].tolist() == want.tolist()
     assert got[4] == 1
+
+
+MIXED_SHAPES = [synth.tiny_z3_code(), synth.random_small_code(4, 5, 12, 8),
+                synth.random_small_code(5, 4, 10, 12)]
+
+
+def _mixed_counters(first, cof):
+    """Frame errors and iteration sum of frames first.. of a mixed batch
+    (code cof[i] for frame first + i), decoded by the oracle per code."""
+    fe = 0
+    it = 0
+    for ci, s in enumerate(MIXED_SHAPES):
+        idx = np.nonzero(cof == ci)[0]
+        if idx.size == 0:
+            continue
+        rc = oracle.RefCode(s.hbm, s.z)
+        for j in idx:
+            f = first + int(j)
+            info = oracle.gen_info(7, f, 1, rc.k)
+            llr = oracle.awgn_llr(rc.encode(info), f, 7, synth.ebn0_db_to_sigma(1.0, rc.k / rc.n))
+            hard, iters, _ = rc.decode_layered_f32(llr, 6, 0.75, True, True, want_post=False)
+            fe += int((oracle.unpack_hard(hard, rc.n)[0, :rc.k] != info[0]).any())
+            it += int(iters[0])
+    return np.array([fe, it, cof.size], dtype=np.int64)
+
+
+def _mixed_worker(rank, world, port, out_path, cof_all):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        first, cof = mixed_shard(cof_all, rank, world)
+        total = reduce_counters(_mixed_counters(first, cof))
+        if rank == 0:
+            np.save(out_path, total)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_mixed_shard_splits_in_order():
+    cof = np.arange(12) % 5
+    parts = [mixed_shard(cof, r, 3) for r in range(3)]
+    assert [p[0] for p in parts] == [0, 4, 8]
+    assert np.concatenate([p[1] for p in parts]).tolist() == cof.tolist()
+    with pytest.raises(ValueError):
+        mixed_shard(cof, 0, 5)
+
+
+def test_two_gloo_ranks_mixed_batch_match_one_process(tmp_path):
+    """Weak-scaled mixed batch: two ranks decode their halves of one global
+    code assignment; the reduced counters equal one process on all frames."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    cof_all = np.random.default_rng(3).integers(0, len(MIXED_SHAPES), 24).astype(np.int32)
+    out = str(tmp_path / "mixed.npy")
+    mp.spawn(_mixed_worker, args=(2, _free_port(), out, cof_all), nprocs=2, join=True)
+    assert np.load(out).tolist() == _mixed_counters(0, cof_all).tolist()
