@@ -391,7 +391,7 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     from paper_2306_12063_gb300 import stats, train
     from paper_2306_12063_gb300.mixed_learned import decode_learned_fallback
     from paper_2306_12063_gb300.shard import reduce_counters
-    from paper_2306_12063_gb300.workload import make_mixed_batch, mixed_frame_id
+    from paper_2306_12063_gb300.workload import make_mixed_batch
 
     shapes = synth.wimax_mixed_set() + [synth.wifi_n648_r12(), synth.wifi_n1944_r56()]
     codes = [ldpc.Code(s.hbm, s.z, device=dev) for s in shapes]
