@@ -519,6 +519,15 @@ ldpc_status ldpc_decode_layered_minsum_noalloc(const int16_t *hbm, int mb, int n
                                                uint32_t *d_hard, int32_t *d_iters,
                                                void *d_post, cudaStream_t stream);
 
+/* Failure-path check (no counterpart in the paper): one warp waits, with
+ * the decoders' bounded wait of `polls` polls (1..2^22), on a bulk-copy
+ * barrier that expects bytes no copy will deliver; the wait gives up, the
+ * kernel sets the code's device status word and returns.  A following
+ * ldpc_sync reports LDPC_ERR_TIMEOUT (and clears the word); the context
+ * stays usable.  Nothing faults, traps or hangs. */
+ldpc_status ldpc_check_bounded_wait(const ldpc_code *code, uint32_t polls,
+                                    cudaStream_t stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *ldpc_last_error(void);
 

@@ -117,6 +117,7 @@ def load(build_if_missing: bool = False):
         "ldpc_mixed_frame_flags": ([vp, vp, vp, vp], i32),
         "ldpc_mixed_move_frames": ([vp, vp, vp, i32, vp, vp, vp], i32),
         "ldpc_mixed_paired_errors": ([vp, vp, vp, vp, vp, vp], i32),
+        "ldpc_check_bounded_wait": ([vp, ctypes.c_uint32, vp], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -375,6 +376,10 @@ class Code:
                                        ctypes.byref(p), _ptr(h_hard), _ptr(h_iters),
                                        _ptr(workspace), int(workspace.numel()),
                                        int(chunk_frames), _stream(stream)))
+
+    def check_bounded_wait(self, polls: int = 4096, stream=None):
+        """Runs the failure-path check; the next sync() raises the timeout."""
+        _check(load().ldpc_check_bounded_wait(self._h, int(polls), _stream(stream)))
 
     def sync(self, timeout_s: float = 60.0, stream=None):
         _check(load().ldpc_sync(self._h, _stream(stream), float(timeout_s)))

@@ -527,6 +527,16 @@ ldpc_status ldpc_decode_host(const ldpc_code *code, ldpc_dtype dtype, const void
     return LDPC_OK;
 }
 
+ldpc_status ldpc_check_bounded_wait(const ldpc_code *code, uint32_t polls,
+                                    cudaStream_t stream) {
+    if (!code) return fail(LDPC_ERR_INVALID_ARG, "ldpc_check_bounded_wait: code is NULL");
+    if (polls < 1 || polls > (1u << 22))
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_check_bounded_wait: polls outside 1..2^22");
+    ldpc_status st = bind(&code->c);
+    if (st) return st;
+    return launch_wait_check(code->c, polls, stream);
+}
+
 ldpc_status ldpc_sync(const ldpc_code *code, cudaStream_t stream, double timeout_s) {
     if (!code) return fail(LDPC_ERR_INVALID_ARG, "ldpc_sync: code is NULL");
     if (!(timeout_s >= 0.0)) return fail(LDPC_ERR_INVALID_ARG, "ldpc_sync: bad timeout");

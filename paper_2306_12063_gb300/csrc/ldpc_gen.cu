@@ -316,6 +316,22 @@ __global__ void paired_kernel(int k, int nwords, const uint8_t *__restrict__ inf
     }
 }
 
+// Failure-path check of the decoders' bounded wait: one warp waits on a
+// bulk-copy barrier that expects bytes no copy will deliver, gives up after
+// `polls` polls, records the timeout in the status word and exits.
+__global__ void wait_check_kernel(int *status, uint32_t polls) {
+    __shared__ uint64_t bar;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(&bar, 16u);   // 16 bytes that never come
+    const bool ok = mbar_wait_bounded(&bar, 0u, polls);
+    if (!__all_sync(0xFFFFFFFFu, ok) && lane == 0) atomicOr(status, kStatusCopyTimeout);
+}
+
 static int grid_for(int64_t work, int threads) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -410,6 +426,12 @@ ldpc_status launch_paired(const Code &c, const uint8_t *d_info, const uint32_t *
         reinterpret_cast<unsigned long long *>(d_counts));
     e = cudaGetLastError();
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "paired_kernel");
+}
+
+ldpc_status launch_wait_check(const Code &c, uint32_t polls, cudaStream_t s) {
+    wait_check_kernel<<<1, 32, 0, s>>>(c.d_status, polls);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "wait_check_kernel");
 }
 
 }  // namespace ldpc

@@ -124,6 +124,7 @@ ldpc_status launch_stats(const Code &c, const uint8_t *d_info, const uint32_t *d
 ldpc_status launch_paired(const Code &c, const uint8_t *d_info, const uint32_t *d_hard_a,
                           const uint32_t *d_hard_b, int64_t frames, int64_t *d_counts,
                           cudaStream_t s);
+ldpc_status launch_wait_check(const Code &c, uint32_t polls, cudaStream_t s);
 // Zeroes the next work-counter slot on stream s and returns it (NULL and an
 // error message on failure).
 unsigned long long *work_slot(const Code &c, cudaStream_t s);
