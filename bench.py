@@ -651,6 +651,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-scale", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=131072,
+                    help="frames per chunk of the end-to-end host pipeline")
     ap.add_argument("--scale-frames", type=int, default=1048576)
     ap.add_argument("--scale-train-steps", type=int, default=300)
     ap.add_argument("--scale-oracle-frames", type=int, default=10000)
@@ -793,17 +795,21 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        host_q = [bt.q.cpu().pin_memory() for bt in batches]
-        h_hard = [torch.empty((F, code.nwords), dtype=torch.int32).pin_memory() for _ in EBN0]
-        h_iters = [torch.empty((F,), dtype=torch.int32).pin_memory() for _ in EBN0]
-        chunk = 32768
+        # the three batches back to back in one pinned buffer (F is a multiple
+        # of 4, so batch b's packed words start at row b F / 4): one pipelined
+        # call per step
+        assert F % 4 == 0
+        host_q = [torch.cat([bt.q for bt in batches]).cpu().pin_memory()]
+        nall = len(EBN0) * F
+        h_hard = [torch.empty((nall, code.nwords), dtype=torch.int32).pin_memory()]
+        h_iters = [torch.empty((nall,), dtype=torch.int32).pin_memory()]
+        chunk = args.e2e_chunk
         wsb = torch.empty(code.host_workspace_bytes(ldpc.I8X4, chunk), dtype=torch.uint8,
                           device=dev)
 
         def e2e_step():
-            for i in range(len(EBN0)):
-                code.decode_host(host_q[i], F, ldpc.I8X4, h_hard[i], h_iters[i], wsb, chunk,
-                                 max_iters=MAX_ITERS, early_stop=True)
+            code.decode_host(host_q[0], nall, ldpc.I8X4, h_hard[0], h_iters[0], wsb, chunk,
+                             max_iters=MAX_ITERS, early_stop=True)
 
         for _ in range(args.warmup):
             e2e_step()
