@@ -533,6 +533,83 @@ def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub):
             "seconds": time.time() - t0}
 
 
+# Tab. 5 of the paper (data-bit throughput, WiMAX N=2304 R=5/6, fixed 10
+# iterations, blocks of 10 codewords per thread): the best float and the best
+# fixed-point (int16, Q_B = 10) rows, both on the 16-core AMD Ryzen 9 5950X.
+PAPER_TAB5 = {"float_32_threads_mtx_mbps": 37.76, "fixed_32_threads_mtx_mbps": 43.95,
+              "hardware": "AMD Ryzen 9 5950X (16 cores / 32 threads), MATLAB R2022a MEX"}
+
+
+def paper_protocol_leg(args, ldpc, torch, dev, stream, barrier, pg):
+    """The paper's throughput protocol (Section 6.2): WiMAX-shaped N=2304
+    R=5/6, a fixed 10 iterations without early stop, plain min-sum (eq. 23):
+    FP32, the paper's int16 wrap-around fixed point, and the int8 decoder;
+    plus the oracle's int16 decoder on the host cores under the same protocol."""
+    sh = synth.wimax_n2304_r56()
+    code = ldpc.Code(sh.hbm, sh.z, device=dev)
+    F = args.paper_frames
+    info = ldpc.gen_info(1, 0, F, code.k, device=dev)
+    cw = code.encode(info)
+    llr = ldpc.awgn_llr(cw, 0, 1, synth.ebn0_db_to_sigma(3.0, code.k / code.n))
+    del cw
+    q16 = ldpc.quantize_i16(llr, 16.0, 10)
+    q8 = ldpc.quantize_pack_i8(llr)
+    hard = torch.empty((F, code.nwords), dtype=torch.int32, device=dev)
+    iters = torch.empty((F,), dtype=torch.int32, device=dev)
+    steps = max(1, args.steps // 2)
+
+    def time_fn(fn):
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = a.elapsed_time(b) / steps
+        if pg is not None:
+            tt = torch.tensor([ms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    out = {"workload": f"WiMAX-shaped N=2304 R=5/6 (seed 3), {F} frames at 3.0 dB, fixed 10 "
+                       "iterations, no early stop, plain min-sum (eq. 23)",
+           "paper_tab5": PAPER_TAB5}
+    cases = (("fp32", ldpc.F32, llr, {}), ("int16_wrap", ldpc.I16W, q16, {}),
+             ("int8", ldpc.I8X4, q8, {"frames": F}))
+    for name, dt, x, kw in cases:
+        ms = time_fn(lambda: code.decode(x, dtype=dt, max_iters=10, normalise=False,
+                                         early_stop=False, out=(hard, iters, None), **kw))
+        g = F * code.k / (ms * 1e-3) / 1e9
+        out[name] = {"value": g, "unit": "Gbit/s", "ms": ms,
+                     "vs_paper_best_fixed": g * 1e3 / PAPER_TAB5["fixed_32_threads_mtx_mbps"]}
+    # the oracle (plain C, one thread per task of 10 codewords) on the host
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    rc = oracle.RefCode(sh.hbm, sh.z)
+    nsmp = args.paper_oracle_frames
+    x16 = q16[:nsmp].cpu().numpy()
+    blocks = [x16[i:i + 10] for i in range(0, nsmp, 10)]
+    threads = os.cpu_count() or 1
+
+    def dec(b):
+        return rc.decode_layered_i16w(b, 10, normalise=False, early_stop=False,
+                                      want_post=False)[1]
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(dec, blocks))
+    secs = time.perf_counter() - t0
+    out["oracle_int16_host"] = {"value": nsmp * rc.k / secs / 1e9, "unit": "Gbit/s",
+                                "cores": threads, "frames": nsmp, "seconds": secs}
+    return out
+
+
 def variants_leg(args, ldpc, torch, dev, stream, barrier, code, batch, pg):
     """The paper's variants timed on the same inputs as the main decoders:
     Section 5's int16 wrap-around decoder and the flooding schedule on the
@@ -651,6 +728,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-scale", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--paper-frames", type=int, default=262144)
+    ap.add_argument("--paper-oracle-frames", type=int, default=40000)
     ap.add_argument("--e2e-chunk", type=int, default=131072,
                     help="frames per chunk of the end-to-end host pipeline")
     ap.add_argument("--scale-frames", type=int, default=1048576)
@@ -842,6 +922,8 @@ def main():
     if not args.no_scale:
         res["learned_scale"] = learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank,
                                                  ws, pg)
+    if not args.no_paper:
+        res["paper_protocol"] = paper_protocol_leg(args, ldpc, torch, dev, stream, barrier, pg)
     if not args.no_variants and not args.no_fp32:
         res["variants"] = variants_leg(args, ldpc, torch, dev, stream, barrier, code, batches[1],
                                        pg)

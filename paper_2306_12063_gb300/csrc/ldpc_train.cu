@@ -341,13 +341,27 @@ int max_smem_optin(int device) {
     return v;
 }
 
-// Frames per block: as many as fit (at most kTrainWarps) under half the
-// opt-in limit, so two blocks can share an SM; 0 if one frame does not fit.
+// Frames per block (1..kTrainWarps): the count that keeps the most frames
+// resident per SM, given the SM's shared memory and the 1 KB each block
+// reserves; ties go to the larger block.  0 if one frame does not fit.
 int warps_for(size_t warp_bytes, int device) {
     const size_t limit = static_cast<size_t>(max_smem_optin(device));
     if (warp_bytes > limit) return 0;
-    int w = static_cast<int>(std::min<size_t>(kTrainWarps, (limit / 2) / warp_bytes));
-    return std::max(w, 1);
+    int per_sm = 0;
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) !=
+        cudaSuccess)
+        per_sm = static_cast<int>(limit);
+    int best = 1, best_frames = 0;
+    for (int w = 1; w <= kTrainWarps; ++w) {
+        const size_t block = w * warp_bytes + 1024;
+        if (w * warp_bytes > limit) break;
+        const int frames = static_cast<int>(static_cast<size_t>(per_sm) / block) * w;
+        if (frames >= best_frames) {
+            best = w;
+            best_frames = frames;
+        }
+    }
+    return best;
 }
 
 ldpc_status check_common(const char *what, const ldpc_code *code, const float *d_llr,
