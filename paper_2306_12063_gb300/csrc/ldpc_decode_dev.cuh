@@ -35,27 +35,40 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
     return r;
 }
-// min(max(a + b, lo), hi) on two 16-bit lanes holding non-negative values
-// (a + b < 65536 per lane); the add and the max issue as one instruction.
-__device__ __forceinline__ uint32_t add_clamp_u16x2(uint32_t a, uint32_t b, uint32_t lo,
-                                                    uint32_t hi) {
-    const uint32_t r = __viaddmax_u16x2(a, b, lo);
-    uint32_t o;
-    asm("min.u16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(hi));
-    return o;
-}
-// Bytes 0, 2 (resp. 1, 3) of x zero-extended into two 16-bit lanes.
+// Byte lanes of x as two 16-bit lanes: bytes 0, 2 (frames 0, 2) or bytes
+// 1, 3 (frames 1, 3), zero-extended (offset-form posteriors, 1..255) or
+// sign-extended (two's-complement messages, -127..127).
 __device__ __forceinline__ uint32_t lanes_even(uint32_t x) { return prmt(x, 0u, 0x4240u); }
 __device__ __forceinline__ uint32_t lanes_odd(uint32_t x) { return prmt(x, 0u, 0x4341u); }
-// Low bytes of the lanes of e (frames 0, 2) and o (frames 1, 3) back into one word.
-__device__ __forceinline__ uint32_t lanes_join(uint32_t e, uint32_t o) { return prmt(e, o, 0x6240u); }
-// Per byte: 0xFF where a < b, for a, b <= 127.
-__device__ __forceinline__ uint32_t lt_mask7(uint32_t a, uint32_t b) {
-    return msb_bytes_to_mask(b + 0x7F7F7F7Fu - a);
+__device__ __forceinline__ uint32_t lanes_even_sx(uint32_t x) { return prmt(x, 0u, 0xA280u); }
+__device__ __forceinline__ uint32_t lanes_odd_sx(uint32_t x) { return prmt(x, 0u, 0xB391u); }
+// min(max(a + b, 1), 255) on two signed 16-bit lanes (|a + b| < 32768):
+// the add and the max issue as one instruction.
+__device__ __forceinline__ uint32_t add_clamp_off16x2(uint32_t a, uint32_t b) {
+    const uint32_t r = __viaddmax_s16x2(a, b, 0x00010001u);
+    uint32_t o;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(0x00FF00FFu));
+    return o;
 }
-// Per byte: 0xFF where x != 0, for x <= 128.
-__device__ __forceinline__ uint32_t nonzero_mask(uint32_t x) {
-    return msb_bytes_to_mask(x + 0x7F7F7F7Fu);
+// 0xFF per byte where bit 7 of the low byte of a lane is set, lanes of e
+// holding frames 0, 2 and lanes of o frames 1, 3: back in frame-byte order.
+__device__ __forceinline__ uint32_t msb_lanes_to_mask(uint32_t e, uint32_t o) {
+    return prmt(e, o, 0xEAC8u);
+}
+// Integer constants that the compiler cannot see through, so that the
+// products and sums below stay multiply-adds (the FMA pipe) instead of being
+// strength-reduced to shifts, adds and logic on the ALU pipe, which bounds
+// the int8 decoder.  z >= 1 for every code, so the result is 1.
+__device__ __forceinline__ uint32_t opaque_one(int z) {
+    uint32_t r;
+    asm("{\n\t.reg .u32 t;\n\tshr.u32 t, %1, 31;\n\txor.b32 %0, t, 1;\n\t}" : "=r"(r) : "r"(z));
+    return r;
+}
+// a * b + c as one multiply-add (b opaque).
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
 }
 // Per byte floor(3 m / 4) = m - ceil(m / 4), m <= 127 (no carry crosses bytes).
 __device__ __forceinline__ uint32_t scale34(uint32_t m) {
@@ -234,20 +247,28 @@ __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint3
 // ---------------------------------------------------------------------------
 // int8 layer, four frames per word.  Posteriors live in shared memory in
 // offset form (Z + 128, one byte per frame, values 1..255) and so does Z_mn
-// inside the row.  The check side works byte-wise: |Z_mn| = |x - 128| (one
-// absolute-difference instruction), the running minimum, second minimum and
-// argmin with compare masks from prmt's sign replication, and the sign
-// parity.  The saturating additions Z_mn = Z_n - L_mn and Z_n = Z_mn + L_mn
-// run on two 16-bit lanes per word (frames 0, 2 and 1, 3) holding
-// non-negative biased values, clamped with packed u16 add-max and min.  The
-// dummy posterior is +127 and the leading slots' stored message sign is
-// kept negative, so their Z_mn clamps to +127: never below a minimum.
+// inside the row; messages are two's-complement bytes.  The saturating
+// additions Z_mn = Z_n - L_mn and Z_n = Z_mn + L_mn run on two 16-bit lanes
+// per word (frames 0, 2 and 1, 3): the zero-extended offset value plus the
+// sign-extended message, clamped to 1..255 with packed s16 add-max and min,
+// is the result in offset form again; the two lane words are joined back
+// into bytes with one multiply-add.  The check side works byte-wise:
+// |Z_mn| = |x - 128| (one absolute-difference instruction), the running
+// minimum and second minimum against compare masks from prmt's sign
+// replication, the sign parity by XOR.  The minima are kept biased by 127
+// per byte so that each compare is one multiply-add; the argmin test of pass
+// 2 likewise.  This moves a third of the row's integer work from the ALU
+// pipe, which bounds the kernel, to the FMA pipe.  The dummy posterior is
+// +127 and the leading slots' stored message sign is kept negative, so
+// their Z_mn clamps to +127: never below a minimum.
 // ---------------------------------------------------------------------------
 template <int DS, int DMAX>
 __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uint32_t *Zs,
                                          uint32_t *rows, int lane, bool norm) {
     constexpr int SGW = sign_words(DMAX);
+    constexpr uint32_t kB = 0x7F7F7F7Fu;   // bias of the running minima
     const int start = DMAX - d;
+    const uint32_t one = opaque_one(c.z), m_one = 0u - one, k256 = one << 8;
     // sign bits forced on for the leading (unused) slots, per sign word
     uint32_t pad[SGW];
 #pragma unroll
@@ -263,72 +284,76 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
         uint32_t SG[SGW];
 #pragma unroll
         for (int k = 0; k < SGW; ++k) SG[k] = rs[3 + k];
-        // offset-128 bytes of -L_old for the four (sign, magnitude) cases
-        const uint32_t P1c = 0x80808080u - M1, P2c = 0x80808080u - M2;   // L > 0
-        const uint32_t N1c = 0x80808080u | M1, N2c = 0x80808080u | M2;   // L < 0
+        // bytes of -L_old for the four (sign, magnitude) cases
+        const uint32_t G1 = (0x80808080u - M1) ^ 0x80808080u;   // L > 0: -M
+        const uint32_t G2 = (0x80808080u - M2) ^ 0x80808080u;
         const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
-        uint32_t off[DMAX], Q[DMAX];
+        uint32_t off[DMAX], QE[DMAX], QO[DMAX], A[DMAX];
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) Q[i] = lds_u32(Zs, off[i]);
-        uint32_t A[DMAX];
-        uint32_t mn1 = 0x7F7F7F7Fu, mn2 = 0x7F7F7F7Fu, sx = 0;
+        for (int i = 0; i < DMAX; ++i) QE[i] = lds_u32(Zs, off[i]);
+        uint32_t mk1 = kB + 0x7F7F7F7Fu, mk2 = kB + 0x7F7F7F7Fu, sx = 0;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
-            const uint32_t u = Q[i];
-            const uint32_t sm = msb_bytes_to_mask(SG[i >> 3] << (7 - (i & 7)));
-            const uint32_t nq = nonzero_mask(IDX ^ (0x01010101u * i));
-            const uint32_t nl = bsel(bsel(P2c, P1c, nq), bsel(N2c, N1c, nq), sm);
-            // (Z + 128) + (128 - L) = Z_mn + 256, clamped to Z_mn in [-127, 127]
-            const uint32_t qe =
-                add_clamp_u16x2(lanes_even(u), lanes_even(nl), 0x00810081u, 0x017F017Fu);
-            const uint32_t qo =
-                add_clamp_u16x2(lanes_odd(u), lanes_odd(nl), 0x00810081u, 0x017F017Fu);
-            const uint32_t x = lanes_join(qe, qo) ^ 0x80808080u;   // offset form of Z_mn
-            Q[i] = x;
-            const uint32_t a = __vabsdiffu4(x, 0x80808080u);       // |Z_mn|
+            const uint32_t u = QE[i];
+            const uint32_t sm = msb_bytes_to_mask(SG[i >> 3] << (7 - (i & 7)));   // L_old < 0
+            // 0xFF where slot i is not the argmin: (IDX ^ i) + 127 has bit 7 set
+            const uint32_t nq = msb_bytes_to_mask(imad(IDX ^ (0x01010101u * i), one, kB));
+            const uint32_t g = bsel(bsel(G2, G1, nq), bsel(M2, M1, nq), sm);      // -L_old
+            // eq. (22): (Z + 128) - L_old, clamped to Z_mn + 128 in 1..255
+            const uint32_t qe = add_clamp_off16x2(lanes_even(u), lanes_even_sx(g));
+            const uint32_t qo = add_clamp_off16x2(lanes_odd(u), lanes_odd_sx(g));
+            QE[i] = qe;
+            QO[i] = qo;
+            const uint32_t x = imad(qo, k256, qe);                   // offset bytes of Z_mn
+            const uint32_t a = __vabsdiffu4(x, 0x80808080u);         // |Z_mn|
             A[i] = a;
-            const uint32_t lt = lt_mask7(a, mn1);
-            const uint32_t tmax = bsel(a, mn1, lt);
-            mn1 = bsel(mn1, a, lt);
-            mn2 = bsel(mn2, tmax, lt_mask7(tmax, mn2));
+            // a < min: bit 7 of (min + 127) - a, no borrow across bytes
+            const uint32_t lt1 = msb_bytes_to_mask(imad(a, m_one, mk1));
+            const uint32_t lt2 = msb_bytes_to_mask(imad(a, m_one, mk2));
+            const uint32_t ak = imad(a, one, kB);
+            mk2 = bsel(bsel(mk2, ak, lt2), mk1, lt1);
+            mk1 = bsel(mk1, ak, lt1);
             sx ^= x;
         }
+        const uint32_t mn1 = mk1 - kB, mn2 = mk2 - kB;
         const uint32_t n1 = norm ? scale34(mn1) : mn1;
         const uint32_t n2 = norm ? scale34(mn2) : mn2;
-        // offset bytes have bit 7 set for Z_mn >= 0: flip once per slot
-        const uint32_t S = (sx ^ ((DMAX & 1) ? 0x80808080u : 0u)) & 0x80808080u;
-        // offset-128 bytes of L_new for the four (sign, magnitude) cases
-        const uint32_t Lp1 = 0x80808080u | n1, Lp2 = 0x80808080u | n2;       // L > 0
-        const uint32_t Ln1 = 0x80808080u - n1, Ln2 = 0x80808080u - n2;       // L < 0
-        uint32_t nsg[SGW];
+        // parity of the negative Z_mn: offset bytes have bit 7 set for
+        // Z_mn >= 0, so flip once per slot
+        const uint32_t P = msb_bytes_to_mask(sx ^ ((DMAX & 1) ? 0x80808080u : 0u));
+        // bytes of L_new by the sign of Z_mn (eq. 23): the message is
+        // negative where Z_mn >= 0 xor the parity is odd
+        const uint32_t h1 = (0x80808080u - n1) ^ 0x80808080u, h2 = (0x80808080u - n2) ^ 0x80808080u;
+        const uint32_t Yp1 = bsel(n1, h1, P), Yp2 = bsel(n2, h2, P);   // Z_mn >= 0
+        const uint32_t Yn1 = bsel(h1, n1, P), Yn2 = bsel(h2, n2, P);   // Z_mn < 0
+        const uint32_t mn1p = mn1 + 0x80808080u;
+        uint32_t zsg[SGW];
 #pragma unroll
-        for (int k = 0; k < SGW; ++k) nsg[k] = pad[k];
+        for (int k = 0; k < SGW; ++k) zsg[k] = 0u;
         uint32_t id = 0;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
-            const uint32_t x = Q[i];
-            const uint32_t nm = msb_bytes_to_mask(~(x ^ S));   // 0xFF: L_new < 0 (S xor Z_mn < 0)
+            const uint32_t pos = msb_lanes_to_mask(QE[i], QO[i]);   // 0xFF: Z_mn >= 0
             // |Z_mn| >= min, so min + 128 - |Z_mn| lies in [1, 128] and equals
             // 128 exactly at the minimum: that edge gets the second minimum (on
             // ties both minima are equal, so any such edge may be the argmin)
-            const uint32_t at_min = msb_bytes_to_mask(mn1 + 0x80808080u - A[i]);
+            const uint32_t at_min = msb_bytes_to_mask(imad(A[i], m_one, mn1p));
             id = bsel(id, 0x01010101u * i, at_min);
-            const uint32_t y = bsel(bsel(Lp1, Lp2, at_min), bsel(Ln1, Ln2, at_min), nm);
-            // (Z_mn + 128) + (L + 128) = Z + 256, clamped to Z in [-127, 127]
-            const uint32_t ze =
-                add_clamp_u16x2(lanes_even(x), lanes_even(y), 0x00810081u, 0x017F017Fu);
-            const uint32_t zo =
-                add_clamp_u16x2(lanes_odd(x), lanes_odd(y), 0x00810081u, 0x017F017Fu);
-            if (i >= start) sts_u32(Zs, off[i], lanes_join(ze, zo) ^ 0x80808080u);
-            nsg[i >> 3] |= nm & ((1u << (i & 7)) * 0x01010101u);
+            const uint32_t y = bsel(bsel(Yn1, Yn2, at_min), bsel(Yp1, Yp2, at_min), pos);
+            // eq. (20): (Z_mn + 128) + L_new, clamped to Z + 128 in 1..255
+            const uint32_t ze = add_clamp_off16x2(QE[i], lanes_even_sx(y));
+            const uint32_t zo = add_clamp_off16x2(QO[i], lanes_odd_sx(y));
+            if (i >= start) sts_u32(Zs, off[i], imad(zo, k256, ze));
+            zsg[i >> 3] |= pos & ((1u << (i & 7)) * 0x01010101u);
         }
         rs[0] = n1;
         rs[1] = n2;
         rs[2] = id;
+        // message sign = not (Z_mn >= 0 xor parity); leading slots negative
 #pragma unroll
-        for (int k = 0; k < SGW; ++k) rs[3 + k] = nsg[k];
+        for (int k = 0; k < SGW; ++k) rs[3 + k] = ~(zsg[k] ^ P) | pad[k];
     }
 }
 
