@@ -179,11 +179,12 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     // kernel's slot class); a layer of degree d fills slots D-d .. D-1 in edge
     // order, so a slot sits at a fixed stride of 32 entries from the row's
     // first one.  Entries are byte offsets into a 4-byte posterior array.  The
-    // unused leading slots point at word N, a dummy posterior holding a value
-    // that cannot affect a row (the decoders run every slot unconditionally);
-    // lanes r >= Z never read the table.
-    std::vector<uint16_t> voff(static_cast<size_t>(mb) * c.rpl * D * 32,
-                               static_cast<uint16_t>(4 * c.n));
+    // unused leading slots of lane l point at word N + l, that lane's own
+    // dummy posterior holding a value that cannot affect a row (the decoders
+    // run every slot unconditionally); lanes r >= Z never read the table.
+    std::vector<uint16_t> voff(static_cast<size_t>(mb) * c.rpl * D * 32);
+    for (size_t q = 0; q < voff.size(); ++q)
+        voff[q] = static_cast<uint16_t>(4 * (c.n + static_cast<int>(q % 32)));
     for (int i = 0; i < mb; ++i) {
         const int d = c.layer_off[i + 1] - c.layer_off[i];
         if (d > D) continue;   // rows above 27 edges are rejected by the decoders

@@ -14,8 +14,8 @@
 // Each kernel is built for a slot class DMAX (8, 12, ..., 27 edge slots per
 // row, the smallest that holds the code's largest row degree) and runs every
 // row as straight-line code over all DMAX slots; a row of degree d fills the
-// last d slots and the leading ones read a dummy posterior that cannot change
-// the row.  Per-edge state (the argmin, the sign bits) is indexed by slot.
+// last d slots and the leading ones read a dummy posterior (one word per
+// lane after Z_n) that cannot change the row.  Per-edge state (the argmin, the sign bits) is indexed by slot.
 //
 // Scheduling.  Frames are handed out by an atomic counter, so a warp whose
 // frame stops early takes the next one.  In the int8 kernel each byte lane
@@ -47,10 +47,10 @@ __global__ void __launch_bounds__(32)
     const int warp = 0, lane = threadIdx.x & 31;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *Zs = smem + 4;
-    uint32_t *rows = Zs + ((c.n + 4) & ~3);   // Z_n words, then the dummy word n
+    uint32_t *rows = Zs + posterior_words(c.n);   // Z_n words, then the per-lane dummy words
     // learned weights of two iterations, [2][mb][wpad(DMAX)], 16-byte aligned
     float *wbuf = reinterpret_cast<float *>(rows + ((c.m * kRowWordsF32 + 3) & ~3));
-    if (lane == 0) Zs[c.n] = 0x7F800000u;   // dummy posterior +inf for unused edge slots
+    Zs[c.n + lane] = 0x7F800000u;   // dummy posterior +inf for unused edge slots
     if (use_bulk) {
         if (lane == 0) {
             mbar_init(bar, 1);
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(32)
     const int warp = 0, lane = threadIdx.x & 31;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *Zs = smem + 4;
-    uint32_t *rows = Zs + ((c.n + 4) & ~3);   // Z_n words, then the dummy word n
+    uint32_t *rows = Zs + posterior_words(c.n);   // Z_n words, then the per-lane dummy words
     const bool norm = p.normalise != 0;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
     const int64_t g0 = blockIdx.x * static_cast<int64_t>(W) + warp;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(32)
             for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i) ^ 0x80808080u;
         }
         for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] = 0u;
-        if (lane == 0) Zs[c.n] = 0xFFFFFFFFu;   // dummy posterior +127 for unused edge slots
+        Zs[c.n + lane] = 0xFFFFFFFFu;   // dummy posterior +127 for unused edge slots
         __syncwarp();
     }
     const int64_t dyn_base = 4 * nwarps;   // frames beyond the initial groups
@@ -155,7 +155,7 @@ static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, in
                                    const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                    void *d_post, cudaStream_t s) {
     const int rw = i8 ? row_words_i8(DMAX) : kRowWordsF32;
-    const int region_words = (((c.n + 4) & ~3) + c.m * rw + 3) & ~3;
+    const int region_words = (posterior_words(c.n) + c.m * rw + 3) & ~3;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -215,7 +215,7 @@ template <int DMAX>
 static ldpc_status launch_learned_t(const Code &c, const float *d_llr, int64_t frames,
                                    const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                    float *d_post, cudaStream_t s) {
-    const int region_words = (((c.n + 4) & ~3) + c.m * kRowWordsF32 + 3) & ~3;
+    const int region_words = (posterior_words(c.n) + c.m * kRowWordsF32 + 3) & ~3;
     const int smem = 16 + (region_words + 2 * c.mb * wpad(DMAX)) * 4;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
@@ -267,7 +267,7 @@ static ldpc_status launch_decode_view_t(const DevCode &dc, bool i8, const void *
                                         int32_t *d_iters, void *d_post,
                                         unsigned long long *work, cudaStream_t s) {
     const int rw = i8 ? row_words_i8(DMAX) : kRowWordsF32;
-    const int region_words = (((dc.n + 4) & ~3) + dc.m * rw + 3) & ~3;
+    const int region_words = (posterior_words(dc.n) + dc.m * rw + 3) & ~3;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -79,10 +79,12 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 // ---------------------------------------------------------------------------
 // Row processing.  Every row runs all DMAX edge slots of its instance as
 // straight-line code (so the compiler can interleave the slots freely); a
-// layer of degree d uses slots DMAX-d .. DMAX-1 and the leading slots read a
-// dummy posterior (word N of the posterior array) whose value leaves the
-// row's minimum, second minimum, sign parity and syndrome unchanged.  Stores
-// are made only for the real slots.  DS is the kernel's slot class (the
+// layer of degree d uses slots DMAX-d .. DMAX-1 and the leading slots of
+// lane l read a dummy posterior (word N + l of the posterior array) whose
+// value leaves the row's minimum, second minimum, sign parity and syndrome
+// unchanged.  Every slot stores (a per-slot store predicate costs an ALU
+// instruction per slot): the FP32 dummy keeps its value under the store,
+// the int8 one is reset once per row.  DS is the kernel's slot class (the
 // offset-table and row-state layout); DMAX <= DS the slots this instance
 // processes.
 // ---------------------------------------------------------------------------
@@ -109,7 +111,7 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
                                           uint32_t *rows, int lane, bool norm, float alpha,
                                           const float *wprev = nullptr,
                                           const float *wcur = nullptr) {
-    const int start = DMAX - d;
+    (void)d;   // leading unused slots run like the others (see the store below)
     float wp[WT ? wpad(DMAX) : 1], wc[WT ? wpad(DMAX) : 1];
     if (WT) {
         // this layer's slots are the last DMAX of the DS staged ones
@@ -172,8 +174,9 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
             // learned weights: w times the signed message
             const uint32_t Lw = WT ? __float_as_uint(__fmul_rn(wc[WT ? i : 0], __uint_as_float(L)))
                                    : L;
-            if (i >= start)
-                sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(Lw))));
+            // unconditional: a leading unused slot stores +inf + L = +inf back
+            // into the dummy posterior
+            sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(Lw))));
             nsg = __funnelshift_l(L, nsg, 1);
         }
         rs[0] = __float_as_uint(n1);
@@ -260,7 +263,8 @@ __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint3
 // 2 likewise.  This moves a third of the row's integer work from the ALU
 // pipe, which bounds the kernel, to the FMA pipe.  The dummy posterior is
 // +127 and the leading slots' stored message sign is kept negative, so
-// their Z_mn clamps to +127: never below a minimum.
+// their Z_mn clamps to +127: never below a minimum.  Their stores change the
+// lane's dummy word, which the lane sets back to +127 after the row.
 // ---------------------------------------------------------------------------
 template <int DS, int DMAX>
 __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uint32_t *Zs,
@@ -345,9 +349,12 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
             // eq. (20): (Z_mn + 128) + L_new, clamped to Z + 128 in 1..255
             const uint32_t ze = add_clamp_off16x2(QE[i], lanes_even_sx(y));
             const uint32_t zo = add_clamp_off16x2(QO[i], lanes_odd_sx(y));
-            if (i >= start) sts_u32(Zs, off[i], imad(zo, k256, ze));
+            sts_u32(Zs, off[i], imad(zo, k256, ze));
             zsg[i >> 3] |= pos & ((1u << (i & 7)) * 0x01010101u);
         }
+        // the leading unused slots stored into this lane's dummy posterior
+        // (word N + lane): back to +127 before the lane's next row reads it
+        Zs[c.n + lane] = 0xFFFFFFFFu;
         rs[0] = n1;
         rs[1] = n2;
         rs[2] = id;

@@ -23,6 +23,11 @@ inline int slot_class(int max_deg) {
     return 0;
 }
 constexpr int kMaxZ = 384;        // 4 N < 65536: byte offsets fit uint16
+// Posterior words in shared memory: Z_n for n < N, then one dummy posterior
+// word per lane (the unused leading edge slots of lane l read word N + l),
+// rounded up to a 16-byte boundary.  4 (N + 31) < 65536 still.
+constexpr int kDummyWords = 32;
+__host__ __device__ constexpr int posterior_words(int n) { return (n + kDummyWords + 3) & ~3; }
 constexpr int kMaxIters = 1000;
 
 // Device status word bits (set by kernels, read and cleared by ldpc_sync).

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(32)
     while (it < n_items) {
         const MixedItem item = items[it];
         const DevCode c = codes[item.code];
-        uint32_t *rows = Zs + ((c.n + 4) & ~3);
+        uint32_t *rows = Zs + posterior_words(c.n);
         float *wbuf = reinterpret_cast<float *>(rows + ((c.m * 3 + 3) & ~3));
         DecodeParams pc = p;
         if (WT) {
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(32)
             pc.max_iters = wT[item.code];
             pc.n_edges = c.n_edges;
         }
-        if (lane == 0) Zs[c.n] = 0x7F800000u;   // dummy posterior of unused edge slots
+        Zs[c.n + lane] = 0x7F800000u;   // dummy posterior of unused edge slots
         __syncwarp();
         for (long long i = item.start; i < item.start + item.count; ++i) {
             const long long uf = uframe[i];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(32)
         const DevCode c = codes[item.code];
         const long long base = ibase[item.code];
         const uint32_t *qc = q + qoff[item.code];
-        uint32_t *rows = Zs + ((c.n + 4) & ~3);
+        uint32_t *rows = Zs + posterior_words(c.n);
         long long end = item.start + item.count;
         long long fr[4];
         int kb[4];
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(32)
                 for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i) ^ 0x80808080u;
             }
             for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] = 0u;
-            if (lane == 0) Zs[c.n] = 0xFFFFFFFFu;   // dummy posterior +127
+            Zs[c.n + lane] = 0xFFFFFFFFu;   // dummy posterior +127
             __syncwarp();
         }
         for (;;) {
@@ -408,12 +408,12 @@ static cudaError_t upload(T **dst, const std::vector<T> &src) {
 }
 
 static int region_bytes_f32(const Code &c) {
-    return 16 + 4 * ((((c.n + 4) & ~3) + c.m * 3 + 3) & ~3);
+    return 16 + 4 * ((posterior_words(c.n) + c.m * 3 + 3) & ~3);
 }
 static int region_bytes_i8(const Code &c, int dslots) {
     const int sw = (dslots + 7) / 8;
     const int rw = (3 + sw + 1) & ~1;
-    return 16 + 4 * ((((c.n + 4) & ~3) + c.m * rw + 3) & ~3);
+    return 16 + 4 * ((posterior_words(c.n) + c.m * rw + 3) & ~3);
 }
 
 // Work items of one group for `chunk` frames per item (int8: a multiple of 4).

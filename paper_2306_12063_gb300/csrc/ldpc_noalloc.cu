@@ -58,8 +58,8 @@ __global__ void noalloc_setup_kernel(HbmArg h, int mb, int nb, int z, int rpl, i
         for (int j = 0; j < nb; ++j) d += h.v[i * nb + j] >= 0;
         const int e = slot - (dslots - d);   // edge index within the row, if any
         const int r = lane + 32 * t;
-        // leading unused slots point at the dummy posterior word N
-        uint16_t val = static_cast<uint16_t>(4 * nb * z);
+        // leading unused slots point at the lane's dummy posterior word N + lane
+        uint16_t val = static_cast<uint16_t>(4 * (nb * z + lane));
         if (e >= 0 && r < z) {
             int seen = 0;
             for (int j = 0; j < nb; ++j) {

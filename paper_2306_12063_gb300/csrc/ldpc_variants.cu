@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(32)
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     uint32_t *Zs = smem;
-    uint32_t *rows = Zs + ((c.n + 4) & ~3);
+    uint32_t *rows = Zs + posterior_words(c.n);
     const bool norm = p.normalise != 0;
-    if (lane == 0) Zs[c.n] = 32767u;   // dummy posterior
+    Zs[c.n + lane] = 32767u;   // dummy posterior
     __syncwarp();
     int64_t f = blockIdx.x;
     while (f < frames) {
@@ -252,9 +252,9 @@ __global__ void __launch_bounds__(32)
     const int n = c.n, z = c.z, E = c.n_edges * c.z;
     float *Z0 = reinterpret_cast<float *>(smem);
     uint32_t *Zn = smem + ((n + 3) & ~3);
-    float *La = reinterpret_cast<float *>(Zn + ((n + 4) & ~3));
+    float *La = reinterpret_cast<float *>(Zn + posterior_words(n));
     float *Lb = La + E;
-    if (lane == 0) Zn[n] = 0x7F800000u;   // dummy posterior for the syndrome table
+    Zn[n + lane] = 0x7F800000u;   // dummy posterior for the syndrome table
     __syncwarp();
     const float alpha = p.normalise ? p.alpha : 1.0f;
     int64_t f = blockIdx.x;
@@ -357,7 +357,7 @@ template <int DMAX>
 ldpc_status launch_i16w_t(const Code &c, const int16_t *llr, int64_t frames,
                           const DecodeParams &p, uint32_t *hard, int32_t *iters, int16_t *post,
                           cudaStream_t s) {
-    const int smem = 4 * (((c.n + 4) & ~3) + c.m * 3);
+    const int smem = 4 * (posterior_words(c.n) + c.m * 3);
     if (smem > smem_optin(c.device))
         return fail(LDPC_ERR_UNSUPPORTED, "decode (int16): code too large for shared memory");
     const void *kern = reinterpret_cast<const void *>(decode_i16w_kernel<DMAX>);
@@ -381,7 +381,7 @@ ldpc_status launch_flooding_t(const Code &c, const float *llr, int64_t frames,
                               const DecodeParams &p, uint32_t *hard, int32_t *iters, float *post,
                               cudaStream_t s) {
     const size_t words =
-        ((c.n + 3) & ~3) + ((c.n + 4) & ~3) + 2 * static_cast<size_t>(c.n_edges) * c.z;
+        ((c.n + 3) & ~3) + posterior_words(c.n) + 2 * static_cast<size_t>(c.n_edges) * c.z;
     const size_t smem = 4 * words;
     if (smem > static_cast<size_t>(smem_optin(c.device)))
         return fail(LDPC_ERR_UNSUPPORTED, "flooding decode: code too large for shared memory");
