@@ -35,19 +35,27 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
     return r;
 }
+// int8 posteriors in shared memory are offset bytes Z + 127 (0..254): bit 7
+// is set exactly where Z >= 1, so it is the complement of the hard decision
+// (eq. 21).  Channel bytes (two's complement, -127..127) convert per byte
+// without borrows: (q xor 128) - 1.
+constexpr uint32_t kDummyI8 = 0xFEFEFEFEu;   // +127
+__device__ __forceinline__ uint32_t to_offset127(uint32_t q) {
+    return (q ^ 0x80808080u) - 0x01010101u;
+}
 // Byte lanes of x as two 16-bit lanes: bytes 0, 2 (frames 0, 2) or bytes
-// 1, 3 (frames 1, 3), zero-extended (offset-form posteriors, 1..255) or
+// 1, 3 (frames 1, 3), zero-extended (offset-form posteriors, 0..254) or
 // sign-extended (two's-complement messages, -127..127).
 __device__ __forceinline__ uint32_t lanes_even(uint32_t x) { return prmt(x, 0u, 0x4240u); }
 __device__ __forceinline__ uint32_t lanes_odd(uint32_t x) { return prmt(x, 0u, 0x4341u); }
 __device__ __forceinline__ uint32_t lanes_even_sx(uint32_t x) { return prmt(x, 0u, 0xA280u); }
 __device__ __forceinline__ uint32_t lanes_odd_sx(uint32_t x) { return prmt(x, 0u, 0xB391u); }
-// min(max(a + b, 1), 255) on two signed 16-bit lanes (|a + b| < 32768):
+// min(max(a + b, 0), 254) on two signed 16-bit lanes (|a + b| < 32768):
 // the add and the max issue as one instruction.
 __device__ __forceinline__ uint32_t add_clamp_off16x2(uint32_t a, uint32_t b) {
-    const uint32_t r = __viaddmax_s16x2(a, b, 0x00010001u);
+    const uint32_t r = __viaddmax_s16x2(a, b, 0u);
     uint32_t o;
-    asm("min.s16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(0x00FF00FFu));
+    asm("min.s16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(0x00FE00FEu));
     return o;
 }
 // 0xFF per byte where bit 7 of the low byte of a lane is set, lanes of e
@@ -249,16 +257,19 @@ __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint3
 
 // ---------------------------------------------------------------------------
 // int8 layer, four frames per word.  Posteriors live in shared memory in
-// offset form (Z + 128, one byte per frame, values 1..255) and so does Z_mn
+// offset form (Z + 127, one byte per frame, values 0..254) and so does Z_mn
 // inside the row; messages are two's-complement bytes.  The saturating
 // additions Z_mn = Z_n - L_mn and Z_n = Z_mn + L_mn run on two 16-bit lanes
 // per word (frames 0, 2 and 1, 3): the zero-extended offset value plus the
-// sign-extended message, clamped to 1..255 with packed s16 add-max and min,
+// sign-extended message, clamped to 0..254 with packed s16 add-max and min,
 // is the result in offset form again; the two lane words are joined back
 // into bytes with one multiply-add.  The check side works byte-wise:
-// |Z_mn| = |x - 128| (one absolute-difference instruction), the running
+// |Z_mn| = |x - 127| (one absolute-difference instruction), the running
 // minimum and second minimum against compare masks from prmt's sign
-// replication, the sign parity by XOR.  The minima are kept biased by 127
+// replication, the sign parity by XOR of bit 7 (set for Z_mn >= 1: a zero
+// Z_mn counts as negative, which changes no message, since it makes the
+// minimum 0 and its own message takes the other edges' signs only).  The
+// minima are kept biased by 127
 // per byte so that each compare is one multiply-add; the argmin test of pass
 // 2 likewise.  This moves a third of the row's integer work from the ALU
 // pipe, which bounds the kernel, to the FMA pipe.  The dummy posterior is
@@ -305,13 +316,13 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
             // 0xFF where slot i is not the argmin: (IDX ^ i) + 127 has bit 7 set
             const uint32_t nq = msb_bytes_to_mask(imad(IDX ^ (0x01010101u * i), one, kB));
             const uint32_t g = bsel(bsel(G2, G1, nq), bsel(M2, M1, nq), sm);      // -L_old
-            // eq. (22): (Z + 128) - L_old, clamped to Z_mn + 128 in 1..255
+            // eq. (22): (Z + 127) - L_old, clamped to Z_mn + 127 in 0..254
             const uint32_t qe = add_clamp_off16x2(lanes_even(u), lanes_even_sx(g));
             const uint32_t qo = add_clamp_off16x2(lanes_odd(u), lanes_odd_sx(g));
             QE[i] = qe;
             QO[i] = qo;
             const uint32_t x = imad(qo, k256, qe);                   // offset bytes of Z_mn
-            const uint32_t a = __vabsdiffu4(x, 0x80808080u);         // |Z_mn|
+            const uint32_t a = __vabsdiffu4(x, 0x7F7F7F7Fu);         // |Z_mn|
             A[i] = a;
             // a < min: bit 7 of (min + 127) - a, no borrow across bytes
             const uint32_t lt1 = msb_bytes_to_mask(imad(a, m_one, mk1));
@@ -324,14 +335,14 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
         const uint32_t mn1 = mk1 - kB, mn2 = mk2 - kB;
         const uint32_t n1 = norm ? scale34(mn1) : mn1;
         const uint32_t n2 = norm ? scale34(mn2) : mn2;
-        // parity of the negative Z_mn: offset bytes have bit 7 set for
-        // Z_mn >= 0, so flip once per slot
+        // parity of the Z_mn <= 0: offset bytes have bit 7 set for
+        // Z_mn >= 1, so flip once per slot
         const uint32_t P = msb_bytes_to_mask(sx ^ ((DMAX & 1) ? 0x80808080u : 0u));
         // bytes of L_new by the sign of Z_mn (eq. 23): the message is
-        // negative where Z_mn >= 0 xor the parity is odd
+        // negative where Z_mn >= 1 xor the parity is odd
         const uint32_t h1 = (0x80808080u - n1) ^ 0x80808080u, h2 = (0x80808080u - n2) ^ 0x80808080u;
-        const uint32_t Yp1 = bsel(n1, h1, P), Yp2 = bsel(n2, h2, P);   // Z_mn >= 0
-        const uint32_t Yn1 = bsel(h1, n1, P), Yn2 = bsel(h2, n2, P);   // Z_mn < 0
+        const uint32_t Yp1 = bsel(n1, h1, P), Yp2 = bsel(n2, h2, P);   // Z_mn >= 1
+        const uint32_t Yn1 = bsel(h1, n1, P), Yn2 = bsel(h2, n2, P);   // Z_mn <= 0
         const uint32_t mn1p = mn1 + 0x80808080u;
         uint32_t zsg[SGW];
 #pragma unroll
@@ -339,14 +350,14 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
         uint32_t id = 0;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
-            const uint32_t pos = msb_lanes_to_mask(QE[i], QO[i]);   // 0xFF: Z_mn >= 0
+            const uint32_t pos = msb_lanes_to_mask(QE[i], QO[i]);   // 0xFF: Z_mn >= 1
             // |Z_mn| >= min, so min + 128 - |Z_mn| lies in [1, 128] and equals
             // 128 exactly at the minimum: that edge gets the second minimum (on
             // ties both minima are equal, so any such edge may be the argmin)
             const uint32_t at_min = msb_bytes_to_mask(imad(A[i], m_one, mn1p));
             id = bsel(id, 0x01010101u * i, at_min);
             const uint32_t y = bsel(bsel(Yn1, Yn2, at_min), bsel(Yp1, Yp2, at_min), pos);
-            // eq. (20): (Z_mn + 128) + L_new, clamped to Z + 128 in 1..255
+            // eq. (20): (Z_mn + 127) + L_new, clamped to Z + 127 in 0..254
             const uint32_t ze = add_clamp_off16x2(QE[i], lanes_even_sx(y));
             const uint32_t zo = add_clamp_off16x2(QO[i], lanes_odd_sx(y));
             sts_u32(Zs, off[i], imad(zo, k256, ze));
@@ -354,20 +365,18 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
         }
         // the leading unused slots stored into this lane's dummy posterior
         // (word N + lane): back to +127 before the lane's next row reads it
-        Zs[c.n + lane] = 0xFFFFFFFFu;
+        Zs[c.n + lane] = kDummyI8;
         rs[0] = n1;
         rs[1] = n2;
         rs[2] = id;
-        // message sign = not (Z_mn >= 0 xor parity); leading slots negative
+        // message sign = not (Z_mn >= 1 xor parity); leading slots negative
 #pragma unroll
         for (int k = 0; k < SGW; ++k) rs[3 + k] = ~(zsg[k] ^ P) | pad[k];
     }
 }
 
-// int8 hard decision per byte: bit 7 set where Z <= 0, i.e. offset value <= 128.
-__device__ __forceinline__ uint32_t hard_bytes_off(uint32_t u) {
-    return ~(u - 0x01010101u) & 0x80808080u;   // u >= 1: no borrow crosses bytes
-}
+// int8 hard decision per byte: bit 7 set where Z <= 0, i.e. offset value <= 127.
+__device__ __forceinline__ uint32_t hard_bytes_off(uint32_t u) { return ~u & 0x80808080u; }
 
 // int8 syndrome over the rows of one layer: bit 7 of byte b set when frame b
 // has an unsatisfied check there.
@@ -381,12 +390,12 @@ __device__ __forceinline__ uint32_t syndrome_rows_i8(const DevCode &c, const uin
         uint32_t off[DMAX];
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
-        // bit 7 of (u - 1) is set iff Z >= 1, so each of the DMAX terms (the
-        // dummy +127 ones included) flips the parity of the hard decisions
+        // bit 7 of u is set iff Z >= 1, so each of the DMAX terms (the dummy
+        // +127 ones included) flips the parity of the hard decisions
         uint32_t par = (DMAX & 1) ? 0x80808080u : 0u;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i)
-            par ^= lds_u32(Zs, off[i]) - 0x01010101u;   // bytes >= 1: no borrow
+            par ^= lds_u32(Zs, off[i]);
         bad |= par;
     }
     return bad;
@@ -464,7 +473,7 @@ __device__ __forceinline__ void write_frame_i8_to(const DevCode &c, const uint32
     if (lane == 0) *it_out = it;
     if (p)
         for (int n = lane; n < c.n; n += 32)
-            p[n] = static_cast<int8_t>(((Zs[n] >> (8 * byte)) & 0xFFu) ^ 0x80u);
+            p[n] = static_cast<int8_t>((((Zs[n] >> (8 * byte)) & 0xFFu) + 1u) ^ 0x80u);
 }
 
 __device__ __forceinline__ void write_frame_i8(const DevCode &c, const uint32_t *Zs, int64_t f,

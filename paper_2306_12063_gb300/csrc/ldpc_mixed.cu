@@ -134,12 +134,12 @@ __global__ void __launch_bounds__(32)
             const uint32_t *src = qc + ((item.start - base) >> 2) * c.n;
             if (use_bulk) {
                 if (!stage_bulk(c, Zs, src, bar, phase, lane)) return;
-                for (int i = lane; i < c.n; i += 32) Zs[i] ^= 0x80808080u;   // offset form
+                for (int i = lane; i < c.n; i += 32) Zs[i] = to_offset127(Zs[i]);
             } else {
-                for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i) ^ 0x80808080u;
+                for (int i = lane; i < c.n; i += 32) Zs[i] = to_offset127(__ldg(src + i));
             }
             for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] = 0u;
-            Zs[c.n + lane] = 0xFFFFFFFFu;   // dummy posterior +127
+            Zs[c.n + lane] = kDummyI8;   // dummy posterior +127
             __syncwarp();
         }
         for (;;) {
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(32)
                                      (static_cast<uint32_t>(4 + (li & 3)) << (4 * b));
                 __syncwarp();
                 for (int i = lane; i < c.n; i += 32)
-                    Zs[i] = prmt(Zs[i], __ldg(src + i) ^ 0x80808080u, sel);
+                    Zs[i] = prmt(Zs[i], to_offset127(__ldg(src + i)), sel);
                 const uint32_t keep = ~(0xFFu << (8 * b));
                 for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] &= keep;
                 __syncwarp();
