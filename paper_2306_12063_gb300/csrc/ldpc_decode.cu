@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(32)
             for (int i = lane; i < c.n; i += 32)
                 Zs[i] = prmt(Zs[i], to_offset127(__ldg(src + i)), sel);
             const uint32_t keep = ~(0xFFu << (8 * b));
-            for (int i = lane; i < c.m * row_words_i8(DMAX); i += 32) rows[i] &= keep;
+            clear_row_minima_i8<DMAX>(rows, c.m, keep, lane);
             __syncwarp();
         }
     }

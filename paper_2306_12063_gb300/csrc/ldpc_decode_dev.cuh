@@ -375,6 +375,23 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
     }
 }
 
+// A refilled byte lane must start with every message zero: clearing its
+// byte of the two stored minima does that (eq. 23 magnitudes 0 give L = 0
+// whatever the argmin and sign bits still hold), at a third of the stores
+// of clearing the whole row state.
+template <int DS>
+__device__ __forceinline__ void clear_row_minima_i8(uint32_t *rows, int m, uint32_t keep,
+                                                    int lane) {
+    static_assert(row_words_i8(DS) % 2 == 0, "rows start 8-byte aligned");
+    for (int r = lane; r < m; r += 32) {
+        uint2 *q = reinterpret_cast<uint2 *>(rows + r * row_words_i8(DS));   // 8-byte aligned
+        uint2 v = *q;
+        v.x &= keep;
+        v.y &= keep;
+        *q = v;
+    }
+}
+
 // int8 hard decision per byte: bit 7 set where Z <= 0, i.e. offset value <= 127.
 __device__ __forceinline__ uint32_t hard_bytes_off(uint32_t u) { return ~u & 0x80808080u; }
 
