@@ -933,10 +933,14 @@ def main():
         threads = os.cpu_count() or 1
         nf = args.cpu_baseline_frames
         bits, secs = run_oracle_sample(nf, 4.0, threads)
+        n1 = max(10, nf // 16)
+        bits1, secs1 = run_oracle_sample(n1, 4.0, 1)
         cpu = {"value": bits / secs / 1e9, "unit": "Gbit/s", "cores": threads,
                "kind": "oracle", "seconds": secs,
                "sample": f"{nf} frames of the 4.0 dB batch, int8, max 20 "
-                         f"iterations, early stop, {threads} threads, blocks of 10 frames"}
+                         f"iterations, early stop, {threads} threads, blocks of 10 frames",
+               "single_thread": {"value": bits1 / secs1 / 1e9, "unit": "Gbit/s",
+                                 "frames": n1, "seconds": secs1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": ws,
