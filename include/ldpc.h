@@ -473,7 +473,8 @@ size_t ldpc_decode_host_workspace_bytes(const ldpc_code *code, ldpc_dtype dtype,
  * chunks of chunk_frames frames, decodes each chunk, and copies hard
  * decisions and iteration counts back, overlapping the copies of one chunk
  * with the decoding of the next on two internal streams ordered after and
- * before `stream`.  Host buffers should be page-locked for the copies to run
+ * before `stream`.  The first chunk is a quarter of chunk_frames (rounded
+ * up to a multiple of 4), so that decoding starts after a short copy.  Host buffers should be page-locked for the copies to run
  * asynchronously.  d_workspace must hold ldpc_decode_host_workspace_bytes.
  * Layouts as in ldpc_decode_layered_minsum (no posteriors). */
 ldpc_status ldpc_decode_host(const ldpc_code *code, ldpc_dtype dtype,

@@ -496,8 +496,10 @@ ldpc_status ldpc_decode_host(const ldpc_code *code, ldpc_dtype dtype, const void
     for (int b = 0; b < 2; ++b)
         LDPC_CUDA_TRY(cudaStreamWaitEvent(c.aux[b], c.ev[0], 0), "cudaStreamWaitEvent");
     int64_t idx = 0;
-    for (int64_t f0 = 0; f0 < frames; f0 += chunk_frames, ++idx) {
-        const int64_t fc = std::min(chunk_frames, frames - f0);
+    // a short first chunk: the pipeline waits only for its copy
+    const int64_t first = std::min(chunk_frames, ((chunk_frames / 4 + 3) / 4) * 4);
+    for (int64_t f0 = 0, fc = 0; f0 < frames; f0 += fc, ++idx) {
+        fc = std::min(idx == 0 ? first : chunk_frames, frames - f0);
         const int b = static_cast<int>(idx & 1);
         cudaStream_t s = c.aux[b];
         char *base = ws + b * (bl + bh + bi);
