@@ -156,6 +156,32 @@ def test_decode_shapes(ldpc, name, dtype):
     _assert_same(*_decode_both(ldpc, s, llr, dtype, 12, True))
 
 
+@pytest.mark.parametrize("name", ["wifi648", "wifi1944", "wimax24_r56"])
+@pytest.mark.parametrize("normalise", [True, False])
+def test_i8_extreme_values(ldpc, name, normalise):
+    """Raw int8 channel values heavy in 0, +-1 and +-127: exact zeros of
+    Z_mn (whose sign the message rule never needs) and saturation on both
+    sides, bit-exact against the oracle."""
+    s = SHAPES[name]
+    rc = oracle.RefCode(s.hbm, s.z)
+    rng = np.random.default_rng(7)
+    F = 61
+    pick = rng.random((F, rc.n))
+    q = rng.integers(-127, 128, (F, rc.n)).astype(np.int8)
+    q[pick < 0.3] = 0
+    q[(pick >= 0.3) & (pick < 0.4)] = 1
+    q[(pick >= 0.4) & (pick < 0.5)] = -1
+    q[(pick >= 0.5) & (pick < 0.6)] = 127
+    q[(pick >= 0.6) & (pick < 0.7)] = -127
+    wh, wi, wp, _ = rc.decode_layered_i8(q, 15, normalise, True)
+    code = ldpc.Code(s.hbm, s.z)
+    words = torch.from_numpy(pack_i8(q).view(np.int32)).cuda()
+    gh, gi, gp = code.decode(words, frames=F, dtype=ldpc.I8X4, max_iters=15,
+                             normalise=normalise, early_stop=True, want_post=True)
+    code.sync()
+    _assert_same((wh, wi, wp), (to_np(gh).view(np.uint32), to_np(gi), to_np(gp)))
+
+
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
 def test_decode_plain_minsum(ldpc, dtype):
     s = SHAPES["wifi648"]
