@@ -322,10 +322,13 @@ def test_frame_stats_match_numpy(ldpc):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
-def test_decode_host_pipeline(ldpc, dtype):
-    """End-to-end entry point on pinned host buffers equals the device call."""
+@pytest.mark.parametrize("frames,chunk", [(1000, 128), (30, 128), (33, 128), (151, 128), (17, 4)])
+def test_decode_host_pipeline(ldpc, dtype, frames, chunk):
+    """End-to-end entry point on pinned host buffers equals the device call,
+    with batches shorter than, equal to and just past the quarter-size first
+    chunk, ragged last chunks and the smallest chunk."""
     s = SHAPES["wifi1944"]
-    _, _, _, llr, _ = oracle_inputs(s, 1000, ebn0=4.0)
+    _, _, _, llr, _ = oracle_inputs(s, frames, ebn0=4.0)
     code = ldpc.Code(s.hbm, s.z)
     F = llr.shape[0]
     if dtype == "f32":
@@ -338,8 +341,8 @@ def test_decode_host_pipeline(ldpc, dtype):
         dt = ldpc.I8X4
     h_hard = torch.empty((F, code.nwords), dtype=torch.int32).pin_memory()
     h_iters = torch.empty((F,), dtype=torch.int32).pin_memory()
-    ws = torch.empty(code.host_workspace_bytes(dt, 128), dtype=torch.uint8, device="cuda")
-    code.decode_host(src, F, dt, h_hard, h_iters, ws, 128, max_iters=20, early_stop=True)
+    ws = torch.empty(code.host_workspace_bytes(dt, chunk), dtype=torch.uint8, device="cuda")
+    code.decode_host(src, F, dt, h_hard, h_iters, ws, chunk, max_iters=20, early_stop=True)
     torch.cuda.synchronize()
     gh, gi, _ = code.decode(dev, frames=F, dtype=dt, max_iters=20, early_stop=True)
     assert (to_np(gi) == h_iters.numpy()).all()
