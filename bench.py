@@ -104,12 +104,26 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/|\s+', re.S)
+
+
+def code_text(src: str) -> str:
+    """C/CUDA source without comments, whitespace runs folded to one space."""
+    def keep(m):
+        t = m.group(0)
+        if t.startswith("//") or t.startswith("/*"):
+            return " "
+        return " " if t.isspace() else t
+    return re.sub(r"\s+", " ", _TOKENS.sub(keep, src)).strip()
+
+
 def kernel_source_digest() -> str:
-    """sha256 (first 16 hex digits) of the decoder kernel sources."""
+    """sha256 (first 16 hex digits) of the decoder kernel sources' code (comments
+    and layout do not count, so a profile stays valid across comment edits)."""
     h = hashlib.sha256()
     for name in ("ldpc_decode.cu", "ldpc_decode_dev.cuh", "ldpc_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2306_12063_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2306_12063_gb300", "csrc", name)) as fh:
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -15,7 +15,8 @@
 // row, the smallest that holds the code's largest row degree) and runs every
 // row as straight-line code over all DMAX slots; a row of degree d fills the
 // last d slots and the leading ones read a dummy posterior (one word per
-// lane after Z_n) that cannot change the row.  Per-edge state (the argmin, the sign bits) is indexed by slot.
+// lane after Z_n) that cannot change the row.  Per-edge state (the argmin,
+// the sign bits) is indexed by slot.
 //
 // Scheduling.  Frames are handed out by an atomic counter, so a warp whose
 // frame stops early takes the next one.  In the int8 kernel each byte lane
@@ -32,7 +33,8 @@ namespace ldpc {
 
 // ---------------------------------------------------------------------------
 // Kernels, one warp per block.  Shared memory: [mbarrier (16 B)][Z_n: N
-// words, 16-byte aligned, the bulk-copy target][row state of all M rows].
+// words, 16-byte aligned, the bulk-copy target, then 32 dummy words][row
+// state of all M rows].
 // With a single warp the posterior array sits at a fixed shared address, so
 // every access is one load or store at the table offset.
 // ---------------------------------------------------------------------------
