@@ -848,7 +848,8 @@ def main():
         st = reduce_counters(st)          # summed over ranks (each decodes its own frames)
         nf = F * ws
         fer[str(eb)] = {"fer": float(st[1]) / nf, "ber": float(st[0]) / (nf * code.k),
-                        "undetected_frames": int(st[2]), "mean_iters": float(st[3]) / nf}
+                        "undetected_frames": int(st[2]), "mean_iters": float(st[3]) / nf,
+                        "iters_hist": [int(x) for x in st[4:]]}
 
     clk = i8_clk or {}
     mhz = clk.get("sm_mhz") or 2070.0

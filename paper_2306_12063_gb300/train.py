@@ -85,21 +85,41 @@ class TrainConfig:
 @dataclass
 class TrainResult:
     weights: object                       # float32[T][nnz_blocks] on the GPU
-    loss_history: object                  # float32[steps] on the GPU
+    loss_history: object                  # float32[steps] on the GPU (this run's steps)
     config: TrainConfig = field(default_factory=TrainConfig)
+    adam_m: object = None                 # Adam first and second moments
+    adam_v: object = None
+    step: int = 0                         # Adam steps taken in total
 
 
 def train_weights(code: Code, cfg: TrainConfig = TrainConfig(), weights=None,
-                  stream=None) -> TrainResult:
+                  stream=None, resume: Optional[TrainResult] = None,
+                  steps: Optional[int] = None) -> TrainResult:
     """Adam on the learned weights; batch b of step s holds frames
-    s * batch .. (s + 1) * batch - 1 of the training streams."""
+    s * batch .. (s + 1) * batch - 1 of the training streams.  `resume`
+    continues from a result (or a loaded checkpoint): its weights, Adam
+    moments and step count; since a step's batch depends on its index only
+    and every kernel is deterministic, stopping and resuming gives the same
+    weights bit for bit as one uninterrupted run.  `steps` (default
+    cfg.steps) ends the run early, counted from the first step."""
     torch = _torch()
     dev = code.device
     B, T, E = cfg.batch, cfg.T, code.nnz_blocks
-    if weights is None:
-        weights = torch.full((T, E), float(cfg.init), dtype=torch.float32, device=dev)
-    m = torch.zeros_like(weights)
-    v = torch.zeros_like(weights)
+    s0 = 0
+    if resume is not None:
+        weights = resume.weights.to(dev).clone()
+        m = resume.adam_m.to(dev).clone()
+        v = resume.adam_v.to(dev).clone()
+        s0 = int(resume.step)
+        if tuple(weights.shape) != (T, E):
+            raise ValueError(f"checkpoint weights {tuple(weights.shape)} do not fit T={T}, "
+                             f"{E} blocks")
+    else:
+        if weights is None:
+            weights = torch.full((T, E), float(cfg.init), dtype=torch.float32, device=dev)
+        m = torch.zeros_like(weights)
+        v = torch.zeros_like(weights)
+    s1 = cfg.steps if steps is None else min(cfg.steps, int(steps))
     info = torch.empty((B, code.k), dtype=torch.uint8, device=dev)
     cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
     sigma = torch.empty((B,), dtype=torch.float32, device=dev)
@@ -107,21 +127,44 @@ def train_weights(code: Code, cfg: TrainConfig = TrainConfig(), weights=None,
     post = torch.empty((T, B, code.n), dtype=torch.float32, device=dev)
     rows = torch.empty((max(T - 1, 0), B, code.m, 4), dtype=torch.int32, device=dev)
     loss = torch.empty((B,), dtype=torch.float32, device=dev)
-    hist = torch.empty((cfg.steps,), dtype=torch.float32, device=dev)
+    hist = torch.empty((max(s1 - s0, 0),), dtype=torch.float32, device=dev)
     gw = torch.empty((T, E), dtype=torch.float32, device=dev)
     ws = torch.empty(max(code.train_workspace_bytes(B, T), 1), dtype=torch.uint8, device=dev)
     rate = code.k / code.n
     scale = 1.0 / (B * code.n)
-    for s in range(cfg.steps):
+    for s in range(s0, s1):
         f0 = s * B
         gen_info(cfg.seed, f0, B, code.k, device=dev, out=info, stream=stream)
         code.encode(info, out=cw, stream=stream)
         snr_sigma(cfg.seed, f0, B, cfg.ebn0_db[0], cfg.ebn0_db[1], rate, device=dev,
                   out=sigma, stream=stream)
         awgn_llr_frames(cw, f0, cfg.seed, sigma, out=llr, stream=stream)
-        code.train_forward(llr, cw, weights, scale, out=(post, rows, loss, hist[s:s + 1]),
-                           stream=stream)
+        code.train_forward(llr, cw, weights, scale,
+                           out=(post, rows, loss, hist[s - s0:s - s0 + 1]), stream=stream)
         code.train_backward(llr, cw, weights, post, rows, scale, workspace=ws, out=(gw, None),
                             stream=stream)
         adam_step(weights, gw, m, v, s + 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, stream=stream)
-    return TrainResult(weights, hist, cfg)
+    return TrainResult(weights, hist, cfg, m, v, max(s1, s0))
+
+
+def save_checkpoint(path: str, result: TrainResult) -> None:
+    """Weights, Adam moments, step count, loss history and configuration as
+    one torch file (tensors moved to the host)."""
+    torch = _torch()
+    torch.save({"weights": result.weights.detach().cpu(),
+                "adam_m": result.adam_m.detach().cpu(),
+                "adam_v": result.adam_v.detach().cpu(),
+                "step": int(result.step),
+                "loss_history": result.loss_history.detach().cpu(),
+                "config": dict(result.config.__dict__)}, path)
+
+
+def load_checkpoint(path: str, device="cpu") -> TrainResult:
+    """A TrainResult from save_checkpoint, its tensors on `device`; pass it
+    as `resume` to continue training."""
+    torch = _torch()
+    d = torch.load(path, map_location="cpu", weights_only=True)
+    cfg = d["config"]
+    cfg["ebn0_db"] = tuple(cfg["ebn0_db"])
+    return TrainResult(d["weights"].to(device), d["loss_history"].to(device), TrainConfig(**cfg),
+                       d["adam_m"].to(device), d["adam_v"].to(device), int(d["step"]))
