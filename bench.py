@@ -766,8 +766,8 @@ def main():
 
     assert torch.cuda.is_available(), "bench.py needs a GPU"
     torch.cuda.set_device(local)
-    if rank == 0 or not os.path.exists(_build.LIB):
-        _build.build()
+    if rank == 0:
+        _build.build()   # the other ranks wait at the barrier below, then load it
     pg = None
     if ws > 1:
         import torch.distributed as dist
