@@ -563,6 +563,9 @@ ldpc_status ldpc_sync(const ldpc_code *code, cudaStream_t stream, double timeout
         LDPC_CUDA_TRY(cudaMemset(code->c.d_status, 0, sizeof(int)), "cudaMemset status");
         if (status & kStatusCopyTimeout)
             return fail(LDPC_ERR_TIMEOUT, "ldpc_sync: a kernel's wait for its bulk copy ran out");
+        if (status & kStatusBadOffset)
+            return fail(LDPC_ERR_CUDA, "ldpc_sync: a kernel read an edge offset outside the "
+                                       "posterior region (debug build check)");
         return fail(LDPC_ERR_CUDA, "ldpc_sync: device status " + std::to_string(status));
     }
     return LDPC_OK;

@@ -29,6 +29,25 @@ __device__ __forceinline__ void sts_u32(uint32_t *base, uint32_t byte_off, uint3
     *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(base) + byte_off) = v;
 }
 
+// Byte offset of an edge's posterior, read from the offset table at p.
+// Debug builds (-DLDPC_DEBUG, the stand-in for a memory checker) check it
+// against the posterior region (N words and the per-lane dummy words, word
+// aligned): an offset outside is recorded in the status word, which
+// ldpc_sync reports, and replaced by the first dummy word, so the access
+// stays in bounds.
+__device__ __forceinline__ uint32_t edge_off(const DevCode &c, const uint16_t *p) {
+    uint32_t o = __ldg(p);
+#ifdef LDPC_DEBUG
+    if (o >= 4u * static_cast<uint32_t>(c.n + kDummyWords) || (o & 3u)) {
+        atomicOr(c.status, kStatusBadOffset);
+        o = 4u * static_cast<uint32_t>(c.n);
+    }
+#else
+    (void)c;
+#endif
+    return o;
+}
+
 // Fixed-width bit helpers (single instructions).
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t r;
@@ -145,7 +164,7 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
         uint32_t off[DMAX];
         float Q[DMAX];
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) Q[i] = __uint_as_float(lds_u32(Zs, off[i]));
         float mn1 = __int_as_float(0x7F800000), mn2 = mn1;
@@ -218,7 +237,7 @@ __device__ __forceinline__ uint32_t syndrome_rows_f32(const DevCode &c, const ui
         const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
         uint32_t off[DMAX];
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
         uint32_t par = 0;
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) {
@@ -305,7 +324,7 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
         const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
         uint32_t off[DMAX], QE[DMAX], QO[DMAX], A[DMAX];
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
 #pragma unroll
         for (int i = 0; i < DMAX; ++i) QE[i] = lds_u32(Zs, off[i]);
         uint32_t mk1 = kB + 0x7F7F7F7Fu, mk2 = kB + 0x7F7F7F7Fu, sx = 0;
@@ -406,7 +425,7 @@ __device__ __forceinline__ uint32_t syndrome_rows_i8(const DevCode &c, const uin
         const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
         uint32_t off[DMAX];
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
         // bit 7 of u is set iff Z >= 1, so each of the DMAX terms (the dummy
         // +127 ones included) flips the parity of the hard decisions
         uint32_t par = (DMAX & 1) ? 0x80808080u : 0u;

@@ -32,6 +32,7 @@ constexpr int kMaxIters = 1000;
 
 // Device status word bits (set by kernels, read and cleared by ldpc_sync).
 constexpr int kStatusCopyTimeout = 1;
+constexpr int kStatusBadOffset = 2;    // debug builds: an edge offset outside Z_n
 
 // Host-side record of a code; the device tables are built once at creation.
 struct Code {

@@ -43,7 +43,7 @@ __device__ __forceinline__ void layer_i16w(const DevCode &c, int layer, uint32_t
         uint32_t off[DMAX];
         int Q[DMAX], A[DMAX];
 #pragma unroll
-        for (int i = 0; i < DMAX; ++i) off[i] = __ldg(vrow + i * 32);
+        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
         int mn1 = 0x7FFFFFFF, mn2 = 0x7FFFFFFF;
         uint32_t sx = 0;
 #pragma unroll
@@ -92,7 +92,7 @@ __device__ __forceinline__ bool syndrome_ok_int(const DevCode &c, const uint32_t
             uint32_t par = 0;
 #pragma unroll
             for (int i = 0; i < DMAX; ++i)
-                par ^= static_cast<int>(lds_u32(Zs, __ldg(vrow + i * 32))) <= 0 ? 1u : 0u;
+                par ^= static_cast<int>(lds_u32(Zs, edge_off(c, vrow + i * 32))) <= 0 ? 1u : 0u;
             bad |= par;
         }
     }
