@@ -499,21 +499,29 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     if rank == 0 and args.scale_oracle_frames > 0:
         out["oracle_subset"] = _oracle_learned_subset(plan, shapes, weights, batch,
                                                       outs["learned_fallback"],
-                                                      args.scale_oracle_frames)
+                                                      args.scale_oracle_frames, first)
     return out
 
 
-def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub):
+def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub, frame_base):
     """The oracle's learned-then-int8-fallback decode of the first nsub frames
-    (thread pool over codes); FER against the GPU pipeline's on the same
-    frames (equal bit for bit)."""
+    (thread pool over codes), on frames the oracle generates itself from the
+    batch's definition (frame j of code c at identity c * 2^32 + frame_base
+    + j); the learned weights, the decoder's parameters, are the ones the GPU
+    trained.  Reports how many of those frames' LLRs equal the GPU batch's,
+    the oracle's FER and how many hard decisions equal the GPU pipeline's."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     nsub = min(nsub, plan.frames)
-    llr = batch.llr[:int(plan.llr_off[nsub])].cpu().numpy()
-    info = batch.info[:int(plan.info_off[nsub])].cpu().numpy()
-    gpu_h = fb_out[0][:int(plan.hard_off[nsub])].cpu().numpy().view(np.uint32)
     cof = plan.code_of_frame[:nsub]
+    info_l, llr_l = oracle.mixed_frames(shapes, cof, LEARNED_EBN0, seed=1,
+                                        frame_base=frame_base)
+    llr = np.concatenate(llr_l)
+    info = np.concatenate(info_l)
+    gpu_llr = batch.llr[:int(plan.llr_off[nsub])].cpu().numpy()
+    inputs_equal = sum(int((gpu_llr[plan.llr_off[f]:plan.llr_off[f + 1]].view(np.uint32) ==
+                            llr_l[f].view(np.uint32)).all()) for f in range(nsub))
+    gpu_h = fb_out[0][:int(plan.hard_off[nsub])].cpu().numpy().view(np.uint32)
 
     def one(ci):
         idx = np.nonzero(cof == ci)[0]
@@ -548,7 +556,7 @@ def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub):
     fe = sum(p[1] for p in parts)
     same = sum(p[2] for p in parts)
     return {"frames": n, "fer": fe / max(n, 1), "frames_equal_to_gpu": same,
-            "seconds": time.time() - t0}
+            "inputs_equal_to_gpu": inputs_equal, "seconds": time.time() - t0}
 
 
 # Tab. 5 of the paper (data-bit throughput, WiMAX N=2304 R=5/6, fixed 10
@@ -610,8 +618,12 @@ def paper_protocol_leg(args, ldpc, torch, dev, stream, barrier, pg):
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     rc = oracle.RefCode(sh.hbm, sh.z)
-    nsmp = args.paper_oracle_frames
-    x16 = q16[:nsmp].cpu().numpy()
+    nsmp = min(args.paper_oracle_frames, F)
+    # the same first frames, generated by the oracle itself (untimed)
+    sig = synth.ebn0_db_to_sigma(3.0, rc.k / rc.n)
+    x16 = oracle.quantize_i16(oracle.awgn_llr(rc.encode(oracle.gen_info(1, 0, nsmp, rc.k)), 0, 1,
+                                              sig), 16.0, 10)
+    same = int((x16 == q16[:nsmp].cpu().numpy()).all())
     blocks = [x16[i:i + 10] for i in range(0, nsmp, 10)]
     threads = os.cpu_count() or 1
 
@@ -624,7 +636,8 @@ def paper_protocol_leg(args, ldpc, torch, dev, stream, barrier, pg):
         list(ex.map(dec, blocks))
     secs = time.perf_counter() - t0
     out["oracle_int16_host"] = {"value": nsmp * rc.k / secs / 1e9, "unit": "Gbit/s",
-                                "cores": threads, "frames": nsmp, "seconds": secs}
+                                "cores": threads, "frames": nsmp, "seconds": secs,
+                                "inputs_equal_to_gpu": bool(same)}
     return out
 
 

@@ -283,7 +283,8 @@ ldpc_status ldpc_adam_step(float *d_param, const float *d_grad, float *d_m, floa
  * Philox4x32-10 at counter {0, f mod 2^32, f / 2^32, 0} under key
  * {seed mod 2^32, (seed / 2^32) ^ 0x534E5253}; then
  * d_sigma[i] = sqrt(1 / (2 rate 10^(Eb/N0 / 10))), computed in double
- * precision and rounded to float. */
+ * precision from the float arguments, each operation rounded once, and
+ * rounded to float. */
 ldpc_status ldpc_snr_sigma(uint64_t seed, int64_t frame0, int64_t frames, float ebn0_lo_db,
                            float ebn0_hi_db, float rate, float *d_sigma, cudaStream_t stream);
 

@@ -9,6 +9,7 @@ use (gcc, -O2 -ffp-contract=off) next to this file.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -291,6 +292,68 @@ def awgn_llr(cw: np.ndarray, frame0: int, seed: int, sigma: float,
                                    float(llr_scale), _ptr(out)),
            "ldpc_ref_awgn_llr")
     return out
+
+
+def snr_sigma(seed: int, frame0: int, frames: int, lo: float, hi: float,
+              rate: float) -> np.ndarray:
+    """Noise level of frames frame0 .. frame0 + frames - 1 of a batch whose
+    Eb/N0 is uniform in [lo, hi) dB per frame: u = (top 24 bits of word 0 of
+    Philox4x32-10 at counter {0, f mod 2^32, f / 2^32, 0} under key
+    {seed mod 2^32, (seed / 2^32) xor 0x534E5253} + 1/2) 2^-24,
+    Eb/N0 = lo + (hi - lo) u, and sigma = sqrt(1 / (2 R 10^(Eb/N0 / 10))) for
+    unit-energy BPSK, evaluated in double precision (each operation rounded
+    once) and rounded to float32.  lo, hi and R are float32 values, as the
+    library's interface takes them."""
+    lo = float(np.float32(lo))
+    hi = float(np.float32(hi))
+    rate = float(np.float32(rate))
+    key = [seed & 0xFFFFFFFF, ((seed >> 32) ^ 0x534E5253) & 0xFFFFFFFF]
+    out = np.empty(frames, dtype=np.float32)
+    for i in range(frames):
+        f = frame0 + i
+        w0 = int(philox4x32_10([0, f & 0xFFFFFFFF, (f >> 32) & 0xFFFFFFFF, 0], key)[0])
+        u = ((w0 >> 8) + 0.5) * 2.0 ** -24
+        ebn0 = lo + (hi - lo) * u
+        out[i] = np.float32(math.sqrt(1.0 / (2.0 * rate * math.pow(10.0, ebn0 / 10.0))))
+    return out
+
+
+def awgn_llr_frames(cw: np.ndarray, frame0: int, seed: int, sigmas) -> np.ndarray:
+    """eq. (16)-(17) with a noise level per frame; frame f's LLR scale is
+    2 / sigma_f^2 in float32 arithmetic (the square, then the quotient, each
+    rounded to float32)."""
+    cw = np.ascontiguousarray(cw, dtype=np.uint8)
+    out = np.empty(cw.shape, dtype=np.float32)
+    for i in range(cw.shape[0]):
+        s = np.float32(sigmas[i])
+        scale = np.float32(2.0) / (s * s)
+        out[i] = awgn_llr(cw[i:i + 1], frame0 + i, seed, float(s), llr_scale=float(scale))[0]
+    return out
+
+
+def mixed_frames(shapes, code_of_frame, ebn0_db=(1.5, 4.5), seed: int = 1,
+                 frame_base: int = 0):
+    """Info bits and channel LLRs of every frame of a mixed batch, in the
+    batch's frame order (lists of uint8[K] and float32[N]): the j-th frame of
+    code c has identity synth.mixed_frame_id(c, frame_base + j) for its info
+    bits, its Eb/N0 draw (uniform in ebn0_db) and its noise."""
+    import synth
+    cof = np.asarray(code_of_frame)
+    info = [None] * cof.size
+    llr = [None] * cof.size
+    for ci, s in enumerate(shapes):
+        idx = np.nonzero(cof == ci)[0]
+        if idx.size == 0:
+            continue
+        rc = RefCode(s.hbm, s.z)
+        f0 = synth.mixed_frame_id(ci, frame_base)
+        inf_c = gen_info(seed, f0, idx.size, rc.k)
+        sig = snr_sigma(seed, f0, idx.size, ebn0_db[0], ebn0_db[1], rc.k / rc.n)
+        x = awgn_llr_frames(rc.encode(inf_c), f0, seed, sig)
+        for j, f in enumerate(idx):
+            info[f] = inf_c[j]
+            llr[f] = x[j]
+    return info, llr
 
 
 def quantize_i8(llr: np.ndarray, scale: float = 4.0, clip: int = 63) -> np.ndarray:

@@ -240,7 +240,8 @@ __global__ void awgn_kernel(const uint8_t *__restrict__ cw, int64_t frame0, int6
 // {0, f mod 2^32, f / 2^32, 0} under key {seed mod 2^32,
 // (seed / 2^32) ^ 0x534E5253}, u = (bits + 1/2) 2^-24; then
 // sigma^2 = 1 / (2 R 10^(Eb/N0 / 10)) (the BPSK Eb/N0 to noise variance
-// relation), evaluated in double precision and rounded to float.
+// relation), evaluated in double precision with every operation rounded on
+// its own (no fused multiply-add) and rounded to float.
 __global__ void snr_sigma_kernel(uint64_t seed, int64_t frame0, int64_t frames, double lo,
                                  double hi, double rate, float *__restrict__ sigma) {
     const uint2 key = make_uint2(static_cast<uint32_t>(seed),
@@ -251,8 +252,9 @@ __global__ void snr_sigma_kernel(uint64_t seed, int64_t frame0, int64_t frames, 
         const uint4 w = philox4x32_10(
             make_uint4(0u, static_cast<uint32_t>(f), static_cast<uint32_t>(f >> 32), 0u), key);
         const double u = (static_cast<double>(w.x >> 8) + 0.5) * 0x1p-24;
-        const double ebn0 = lo + (hi - lo) * u;
-        sigma[i] = static_cast<float>(sqrt(1.0 / (2.0 * rate * pow(10.0, ebn0 / 10.0))));
+        const double ebn0 = __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), u));
+        const double p = pow(10.0, __ddiv_rn(ebn0, 10.0));
+        sigma[i] = static_cast<float>(__dsqrt_rn(__ddiv_rn(1.0, __dmul_rn(__dmul_rn(2.0, rate), p))));
     }
 }
 

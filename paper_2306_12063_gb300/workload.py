@@ -43,8 +43,8 @@ class MixedBatch:
 
 def mixed_frame_id(code_index: int, j: int) -> int:
     """Frame identity of the j-th frame of code `code_index` in a mixed batch
-    (the counter of its info bits, noise and Eb/N0 draws)."""
-    return (int(code_index) << 32) + int(j)
+    (the counter of its info bits, noise and Eb/N0 draws; synth's rule)."""
+    return synth.mixed_frame_id(code_index, j)
 
 
 def make_mixed_batch(plan, ebn0_db=(1.5, 4.5), seed: int = 1, frame_base: int = 0,

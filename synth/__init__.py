@@ -266,6 +266,13 @@ def mixed_frame_assignment(n_codes: int, frames: int, seed: int = 3):
     return idx, ebn0
 
 
+def mixed_frame_id(code_index: int, j: int) -> int:
+    """Identity of the j-th frame of code `code_index` in a mixed batch: the
+    counter of its info-bit, noise and Eb/N0 draws (code index in the high
+    32 bits, so the codes' streams never overlap)."""
+    return (int(code_index) << 32) + int(j)
+
+
 def ebn0_db_to_sigma(ebn0_db: float, rate: float) -> float:
     """Noise standard deviation for BPSK with unit symbol energy at the given
     Eb/N0 and code rate: sigma^2 = 1 / (2 R 10^(Eb/N0 / 10)).  The paper does

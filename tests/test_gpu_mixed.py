@@ -32,6 +32,9 @@ def _shapes():
 
 
 def _setup(ldpc, shapes, frames, seed, ebn0=(1.5, 4.5)):
+    """GPU batch of the plan, checked bit for bit against the same frames
+    generated by the oracle; the oracle's own frames (info, LLRs in the
+    plan's layout) are what the oracle decodes below."""
     from paper_2306_12063_gb300.workload import make_mixed_batch
     codes = [ldpc.Code(s.hbm, s.z) for s in shapes]
     cs = ldpc.CodeSet(codes)
@@ -39,6 +42,13 @@ def _setup(ldpc, shapes, frames, seed, ebn0=(1.5, 4.5)):
     cof = rng.integers(0, len(shapes), frames).astype(np.int32)
     plan = ldpc.MixedPlan(cs, cof)
     batch = make_mixed_batch(plan, ebn0)
+    info, llr = oracle.mixed_frames(shapes, cof, ebn0)
+    ref_llr = np.concatenate(llr)
+    ref_info = np.concatenate(info)
+    got = batch.llr.cpu().numpy()[:ref_llr.size]
+    assert (got.view(np.uint32) == ref_llr.view(np.uint32)).all()
+    assert (batch.info.cpu().numpy()[:ref_info.size] == ref_info).all()
+    batch.ref_llr, batch.ref_info = ref_llr, ref_info
     return codes, cs, plan, batch
 
 
@@ -83,7 +93,7 @@ def test_mixed_bit_exact_against_oracle(ldpc, dtype):
     else:
         d_in, dt = plan.quantize(batch.llr), ldpc.I8X4
     hard, iters, post = plan.decode(d_in, dt, max_iters=20, want_post=True)
-    ref = _oracle_per_code(shapes, plan, batch.llr.cpu().numpy(), dtype, 20)
+    ref = _oracle_per_code(shapes, plan, batch.ref_llr, dtype, 20)
     _check_frames(plan, ref, hard, iters, post)
     # after autotuning (other work-item sizes and residency caps) still exact
     plan.autotune(d_in, dt, max_iters=20, reps=1)
@@ -102,12 +112,12 @@ def test_mixed_unaligned_codes_and_single_code(ldpc):
         d_in = batch.llr if dtype == "f32" else plan.quantize(batch.llr)
         dt = ldpc.F32 if dtype == "f32" else ldpc.I8X4
         hard, iters, post = plan.decode(d_in, dt, max_iters=12, want_post=True)
-        ref = _oracle_per_code(shapes, plan, batch.llr.cpu().numpy(), dtype, 12)
+        ref = _oracle_per_code(shapes, plan, batch.ref_llr, dtype, 12)
         _check_frames(plan, ref, hard, iters, post)
     one = [synth.wimax_mixed_set()[40]]
     codes, cs, plan, batch = _setup(ldpc, one, 33, seed=2)
     hard, iters, post = plan.decode(batch.llr, ldpc.F32, max_iters=20, want_post=True)
-    ref = _oracle_per_code(one, plan, batch.llr.cpu().numpy(), "f32", 20)
+    ref = _oracle_per_code(one, plan, batch.ref_llr, "f32", 20)
     _check_frames(plan, ref, hard, iters, post)
 
 
@@ -119,7 +129,7 @@ def test_mixed_stats_and_graph(ldpc):
     cnt, fe = plan.stats(batch.info, hard, iters, 20)
     # per-code frame errors from the unpacked hard decisions
     hw = hard.cpu().numpy().view(np.uint32)
-    info = batch.info.cpu().numpy()
+    info = batch.ref_info
     want = np.zeros(len(shapes), dtype=np.int64)
     for f in range(plan.frames):
         c = codes[plan.code_of_frame[f]]
@@ -156,7 +166,7 @@ def test_mixed_learned_and_fallback(ldpc):
     plan.set_weights([torch.from_numpy(w).cuda() for w in ws])
     hard, iters, post = plan.decode_learned(batch.llr, early_stop=True, want_post=True)
     fb_hard, fb_iters, nfb = decode_learned_fallback(plan, batch.llr)
-    llr_h = batch.llr.cpu().numpy()
+    llr_h = batch.ref_llr
     hw, it, pw = hard.cpu().numpy().view(np.uint32), iters.cpu().numpy(), post.cpu().numpy()
     fhw, fit = fb_hard.cpu().numpy().view(np.uint32), fb_iters.cpu().numpy()
     bad_total = 0
@@ -187,7 +197,7 @@ def test_mixed_learned_and_fallback(ldpc):
     flags = plan.frame_flags(hard).cpu().numpy()
     assert flags.sum() == bad_total
     cnt = plan.paired_errors(batch.info, hard, fb_hard).cpu().numpy()
-    info = batch.info.cpu().numpy()
+    info = batch.ref_info
     wa = np.zeros(plan.frames, bool)
     wb = np.zeros(plan.frames, bool)
     for f in range(plan.frames):

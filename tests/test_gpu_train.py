@@ -168,28 +168,21 @@ def test_single_iteration_and_empty_batch(ldpc):
 
 
 def test_snr_sigma_and_per_frame_channel(ldpc):
-    seed, f0, F, lo, hi, rate = 77, 1234, 300, 1.0, 4.0, 0.5
+    """Per-frame Eb/N0 draws and the per-frame-sigma channel equal the
+    oracle's, bit for bit."""
+    seed, f0, F, lo, hi, rate = 77, 1234, 20000, 1.0, 4.0, 0.5
     sig = ldpc.snr_sigma(seed, f0, F, lo, hi, rate).cpu().numpy()
-    key = [seed & 0xFFFFFFFF, (seed >> 32) ^ 0x534E5253]
-    want = []
-    for i in range(F):
-        f = f0 + i
-        x = oracle.philox4x32_10([0, f & 0xFFFFFFFF, f >> 32, 0], key)[0]
-        u = ((int(x) >> 8) + 0.5) * 2.0 ** -24
-        e = lo + (hi - lo) * u
-        want.append(np.sqrt(1.0 / (2 * rate * 10 ** (e / 10))))
-    np.testing.assert_allclose(sig, np.array(want), rtol=1e-7)
+    want = oracle.snr_sigma(seed, f0, F, lo, hi, rate)
+    assert (sig.view(np.uint32) == want.view(np.uint32)).all()
     shape = synth.wifi_n648_r12()
     rc = oracle.RefCode(shape.hbm, shape.z)
+    F = 300
     info = oracle.gen_info(seed, f0, F, rc.k)
     cw = rc.encode(info)
     got = ldpc.awgn_llr_frames(torch.from_numpy(cw).cuda(), f0, seed,
-                               torch.from_numpy(sig).cuda()).cpu().numpy()
-    for i in range(0, F, 37):
-        s = np.float32(sig[i])
-        scale = np.float32(2.0) / (s * s)
-        ref = oracle.awgn_llr(cw[i:i + 1], f0 + i, seed, float(s), llr_scale=float(scale))
-        assert (got[i] == ref[0]).all()
+                               torch.from_numpy(want[:F].copy()).cuda()).cpu().numpy()
+    ref = oracle.awgn_llr_frames(cw, f0, seed, want[:F])
+    assert (got.view(np.uint32) == ref.view(np.uint32)).all()
 
 
 def test_adam_step(ldpc):

@@ -82,3 +82,43 @@ def test_info_bits_counter_layout():
     assert [full[128 + t] for t in range(128)] == [bit(t) for t in range(128)]
     big = oracle.gen_info(7, 0, 64, 1620)
     assert abs(big.mean() - 0.5) < 0.01
+
+
+# ------------------------------------------------ per-frame Eb/N0 and channel
+
+def test_snr_sigma_range_uniformity_and_counter():
+    """Eb/N0 recovered from each sigma lies in [lo, hi) and is uniform there
+    (Kolmogorov-Smirnov); a frame's draw depends on its index only."""
+    from scipy import stats
+    lo, hi, rate = 1.0, 4.0, 5 / 6
+    sig = oracle.snr_sigma(9, 1000, 20000, lo, hi, rate).astype(np.float64)
+    ebn0 = 10 * np.log10(1.0 / (2 * rate * sig ** 2))
+    assert ebn0.min() >= lo - 1e-5 and ebn0.max() < hi + 1e-5
+    assert stats.kstest((ebn0 - lo) / (hi - lo), "uniform").pvalue > 1e-3
+    assert (oracle.snr_sigma(9, 1003, 10, lo, hi, rate) ==
+            oracle.snr_sigma(9, 1000, 13, lo, hi, rate)[3:]).all()
+    assert not (oracle.snr_sigma(10, 1000, 50, lo, hi, rate) ==
+                oracle.snr_sigma(9, 1000, 50, lo, hi, rate)).any()
+
+
+def test_snr_sigma_degenerate_range_is_the_closed_form():
+    for db, rate in ((2.0, 0.5), (4.5, 0.75), (-1.0, 0.625)):   # exact in float32
+        sig = oracle.snr_sigma(3, 0, 7, db, db, rate)
+        assert (sig == np.float32(synth.ebn0_db_to_sigma(db, rate))).all()
+
+
+def test_mixed_frames_identities_and_codewords():
+    """Frame j of code c is drawn at identity c * 2^32 + j; every codeword
+    satisfies H c = 0, and at a very high Eb/N0 the LLR signs are the bits."""
+    shapes = [synth.tiny_z2_code(), synth.tiny_z3_code(), synth.wifi_n648_r12()]
+    cof = np.array([2, 0, 1, 1, 2, 0, 2, 1], dtype=np.int32)
+    info, llr = oracle.mixed_frames(shapes, cof, (40.0, 40.0), seed=5)
+    seen = {0: 0, 1: 0, 2: 0}
+    for f, c in enumerate(cof):
+        rc = oracle.RefCode(shapes[c].hbm, shapes[c].z)
+        j = seen[int(c)]
+        seen[int(c)] += 1
+        assert (info[f] == oracle.gen_info(5, (int(c) << 32) + j, 1, rc.k)[0]).all()
+        cw = rc.encode(info[f][None])[0]
+        assert rc.syndrome_weight(cw) == 0
+        assert ((llr[f] < 0) == (cw == 1)).all()
