@@ -15,6 +15,26 @@
  *   Packed hard bits: bit (n % 32) of word n / 32, words [F][ceil(N/32)].
  *
  * Every function returns 0 on success or a positive status code.
+ *
+ * Pins (CPU tests that fix each part against the paper or the mathematics,
+ * not against itself):
+ *   code set-up, encoder: H c^T = 0 over the explicit H, systematic form,
+ *     linearity, equality with a textbook GF(2) elimination, the hand-worked
+ *     Z = 2 example (tests/test_oracle_encoder.py, tests/golden/);
+ *   Philox, Box-Muller, channel, quantisers: published known-answer vectors,
+ *     distribution and rounding properties (tests/test_oracle_channel.py);
+ *   layered FP32 / int8 decoders: the hand-worked Z = 2 traces, one-iteration
+ *     recovery of noiseless input, single-parity-check ML, brute-force ML
+ *     bounds, FP32 = int8 where nothing saturates, the counted saturations
+ *     (tests/test_oracle_decoder.py);
+ *   weighted (learned) decoder: the worked example with weights, constant
+ *     weights = the alpha decoder (tests/test_oracle_decoder.py);
+ *   flooding: equal to layered on one layer (tests/test_oracle_decoder.py);
+ *   int16 wrap decoder, bitmap encoder: hand-worked overflow traces, FP32 /
+ *     int8 equivalence without overflow, brute-force rotation, the byte
+ *     encoder (tests/test_oracle_variants.py, tests/golden/).
+ * FER values of the seeded stand-in codes are parity unpinned: the standard
+ * matrices and the paper's reference decoder are not available.
  */
 #ifndef LDPC_ORACLE_H
 #define LDPC_ORACLE_H
