@@ -940,7 +940,20 @@ def main():
             tt = torch.tensor([e_ms], device=dev)
             pg.all_reduce(tt, op=pg.ReduceOp.MAX)
             e_ms = float(tt.item())
+        # the box's pinned host-to-device copy rate, beside the number: the
+        # host link is shared with the machine's other GPUs
+        probe = host_q[0].view(-1)[: (256 << 20) // 4]
+        probe_d = torch.empty_like(probe, device=dev)
+        probe_d.copy_(probe, non_blocking=True)
+        a.record(stream)
+        for _ in range(3):
+            probe_d.copy_(probe, non_blocking=True)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * probe.numel() * 4 / (a.elapsed_time(b_) * 1e-3) / 1e9
+        del probe_d
         e2e = {"value": bits_per_step * e_steps / (e_ms * 1e-3) / 1e9, "unit": "Gbit/s",
+               "h2d_copy_gbs": h2d_gbs,
                "h2d_bytes_per_step": sum(int(h.numel()) * 4 for h in host_q),
                "d2h_bytes_per_step": sum(int(h.numel()) * 4 for h in h_hard) +
                sum(int(h.numel()) * 4 for h in h_iters),
