@@ -97,3 +97,39 @@ def test_symbols_parsed_from_header():
     for must in ("ldpc_code_create", "ldpc_encode", "ldpc_decode_layered_minsum",
                  "ldpc_quantize_pack_i8", "ldpc_last_error"):
         assert must in names
+
+
+def test_newer_entry_points_check_arguments_on_the_host(lib):
+    """Per-frame Eb/N0 and channel, Adam, learned decoding and training,
+    mixed plans, the paper variants, the host pipeline and the bounded-wait
+    check refuse bad arguments with LDPC_ERR_INVALID_ARG before any device
+    work, and zero-sized work succeeds without buffers."""
+    p = ldpc._Params(10, 0.75, 1, 0)
+    out = ctypes.c_void_p()
+    bad = [
+        lib.ldpc_snr_sigma(1, 0, 4, 1.0, 4.0, 0.0, None, None),         # rate 0
+        lib.ldpc_snr_sigma(1, 0, 4, 5.0, 4.0, 0.5, None, None),         # lo > hi
+        lib.ldpc_snr_sigma(1, 0, -1, 1.0, 4.0, 0.5, None, None),        # negative count
+        lib.ldpc_snr_sigma(1, 0, 4, 1.0, 4.0, 0.5, None, None),         # NULL output
+        lib.ldpc_awgn_llr_frames(None, 0, 4, 10, 1, None, None, None),
+        lib.ldpc_adam_step(None, None, None, None, -1, 1, 1e-3, 0.9, 0.999, 1e-8, None),
+        lib.ldpc_adam_step(None, None, None, None, 4, 0, 1e-3, 0.9, 0.999, 1e-8, None),
+        lib.ldpc_decode_learned_minsum(None, None, 4, None, 8, 1, None, None, None, None),
+        lib.ldpc_learned_train_forward(None, None, None, 4, None, 8, None, None, None, 1.0,
+                                       None, None),
+        lib.ldpc_codeset_create(None, 0, ctypes.byref(out)),
+        lib.ldpc_mixed_plan_create(None, None, 4, ctypes.byref(out)),
+        lib.ldpc_decode_mixed(None, 0, None, ctypes.byref(p), None, None, None, None),
+        lib.ldpc_mixed_autotune(None, 0, None, ctypes.byref(p), None, None, 3, None),
+        lib.ldpc_quantize_i16(None, None, 4, 16.0, 10, None),
+        lib.ldpc_encode_bitmap(None, None, None, 4, None),
+        lib.ldpc_decode_flooding_minsum(None, None, 4, ctypes.byref(p), None, None, None, None),
+        lib.ldpc_decode_host(None, 0, None, 4, ctypes.byref(p), None, None, None, 0, 4, None),
+        lib.ldpc_paired_frame_errors(None, None, None, None, 4, None, None),
+        lib.ldpc_check_bounded_wait(None, 100, None),
+    ]
+    assert bad == [1] * len(bad), bad
+    assert out.value is None
+    assert lib.ldpc_snr_sigma(1, 0, 0, 1.0, 4.0, 0.5, None, None) == 0
+    assert lib.ldpc_awgn_llr_frames(None, 0, 0, 10, 1, None, None, None) == 0
+    assert lib.ldpc_adam_step(None, None, None, None, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == 0
