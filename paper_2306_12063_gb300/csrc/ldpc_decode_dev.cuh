@@ -288,10 +288,10 @@ __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint3
 // replication, the sign parity by XOR of bit 7 (set for Z_mn >= 1: a zero
 // Z_mn counts as negative, which changes no message, since it makes the
 // minimum 0 and its own message takes the other edges' signs only).  The
-// minima are kept biased by 127
-// per byte so that each compare is one multiply-add; the argmin test of pass
-// 2 likewise.  This moves a third of the row's integer work from the ALU
-// pipe, which bounds the kernel, to the FMA pipe.  The dummy posterior is
+// minima are kept biased by 127 per byte so that each compare is one
+// multiply-add; the argmin test of pass 2 likewise.  This moves a third of
+// the row's integer work from the ALU pipe, which bounds the kernel, to the
+// FMA pipe.  The dummy posterior is
 // +127 and the leading slots' stored message sign is kept negative, so
 // their Z_mn clamps to +127: never below a minimum.  Their stores change the
 // lane's dummy word, which the lane sets back to +127 after the row.
