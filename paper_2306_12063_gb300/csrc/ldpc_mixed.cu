@@ -976,12 +976,51 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
         *ms = t[t.size() / 2];
         return LDPC_OK;
     };
+    // median of `reps` timed launches of one group alone: a group's chunk
+    // moves its own time, which the whole batch's noise can hide when the
+    // group's share is small
+    auto measure_group = [&](int gi, float *ms) -> ldpc_status {
+        std::vector<float> t;
+        for (int r = 0; r < reps; ++r) {
+            cudaEventRecord(a, stream);
+            ldpc_status s2 = launch_group(p, gi, dt, d_in, dp, d_hard, d_iters, nullptr, stream);
+            if (s2 != LDPC_OK) return s2;
+            cudaEventRecord(b, stream);
+            cudaError_t e2 = cudaEventSynchronize(b);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "ldpc_mixed_autotune");
+            float x = 0;
+            cudaEventElapsedTime(&x, a, b);
+            t.push_back(x);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return LDPC_OK;
+    };
     const std::vector<int> chunks = dt == 0 ? std::vector<int>{1, 2, 4, 8, 16, 32}
                                             : std::vector<int>{4, 8, 16, 32, 64, 128};
     st = launch_all(p, dt, d_in, dp, d_hard, d_iters, nullptr, stream);   // warm-up
+    // each group's chunk, timed on the group alone
+    for (size_t gi = 0; st == LDPC_OK && gi < p.groups.size(); ++gi) {
+        MixedGroup &g = p.groups[gi];
+        float gbest = 0;
+        st = measure_group(static_cast<int>(gi), &gbest);
+        for (int ch : chunks) {
+            if (st != LDPC_OK) break;
+            if (ch == g.chunk[dt]) continue;
+            const int old = g.chunk[dt];
+            g.chunk[dt] = ch;
+            float ms = 0;
+            st = measure_group(static_cast<int>(gi), &ms);
+            if (st != LDPC_OK) break;
+            if (ms < gbest) gbest = ms;
+            else g.chunk[dt] = old;
+        }
+    }
     float best = 0;
     if (st == LDPC_OK) st = measure(&best);
-    // coordinate descent: each group's chunk, then its residency cap
+    // then, on the whole batch (where the groups run beside one another),
+    // coordinate descent from there: each group's chunk, then its residency
+    // cap (caps trade one group's speed for room for the others)
     for (size_t gi = 0; st == LDPC_OK && gi < p.groups.size(); ++gi) {
         MixedGroup &g = p.groups[gi];
         for (int ch : chunks) {
