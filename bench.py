@@ -41,11 +41,12 @@ METRIC_BASIS = ("value: info Gbit/s of the plain int8 layered min-sum decoder on
                 "roofline.frac; learned-NMS against plain min-sum at matched FER: the "
                 "learned (N=648) and learned_scale (mixed set) objects")
 # Algorithmic operations per edge per iteration (per frame, or per packed
-# word of four frames): pass 1 = 9 (message rebuild 2, subtract, abs, min1,
-# max, min2, argmin, sign xor), pass 2 = 4 (select, sign, add, sign store),
-# syndrome = 2 (hard decision, xor); per row per iteration 4 (two scalings,
-# sign extraction, state store).
-OPS_PER_EDGE = 13 + 2
+# word of four frames), the scope table's count: pass 1 = 9 (old message
+# rebuilt by a select and a sign, subtract, |.|, two compare/select pairs for
+# the two minima and the argmin, sign xor); pass 2 = 3 (select, sign, add);
+# syndrome = 1 (xor).  Shared-memory accesses are not counted.  Per row per
+# iteration: two scalings, the sign extraction and the state store (4).
+OPS_PER_EDGE = 13
 OPS_PER_ROW = 4
 SMS = 152
 LANES_PER_SM = 128
@@ -738,6 +739,94 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- profiling
+
+def profile_cases():
+    """Small, reproducible cases that launch each decoder-family kernel exactly
+    once (after generating its inputs), for a kernel profiler's name filter
+    (``python bench.py --profile-cases``):
+
+    1. learned FP32 decoder (`decode_f32_kernel<8, true>`), N=648, 65,536 frames,
+       T = 8, weights 0.8, Eb/N0 uniform in [1.5, 4.5) dB;
+    2. mixed int8 and FP32 decoders (`mixed_i8_kernel`, `mixed_f32_kernel`) on
+       the four R=3/4 WiMAX-shaped codes with Z = 84..96 (one launch group),
+       65,536 frames;
+    3. Section 5 int16 wrap-around decoder (`decode_i16w_kernel`), N=1944,
+       65,536 frames at 4.0 dB;
+    4. flooding FP32 decoder (`decode_flooding_kernel`), N=648, 16,384 frames,
+       10 iterations;
+    5. Alg. A1 bitmap encoder (`encode_bitmap_kernel`), N=2304 R=5/6, 262,144
+       frames;
+    6. one training step (`train_forward_kernel`, `train_backward_kernel`),
+       N=648, batch 4,096, T = 8.
+
+    Every input is generated on the GPU by the library's own kernels first
+    (those kernels are not among the names above).
+    """
+    import torch
+
+    import synth
+    from paper_2306_12063_gb300 import (F32, I8X4, I16W, Code, CodeSet, MixedPlan, awgn_llr,
+                                        awgn_llr_frames, gen_info, load, quantize_i16,
+                                        snr_sigma, _build)
+    from paper_2306_12063_gb300.workload import make_mixed_batch
+
+    _build.build()
+    load()
+    dev = "cuda"
+    # 1. learned decoder
+    s648 = synth.wifi_n648_r12()
+    c648 = Code(s648.hbm, s648.z)
+    F = 65536
+    info = gen_info(1, 0, F, c648.k)
+    cw = c648.encode(info)
+    sig = snr_sigma(1, 0, F, 1.5, 4.5, 0.5)
+    llr648 = awgn_llr_frames(cw, 0, 1, sig)
+    w = torch.full((8, c648.nnz_blocks), 0.8, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    c648.decode_learned(llr648, w, early_stop=True)
+    torch.cuda.synchronize()
+    # 2. mixed batch, one launch group
+    shapes = [s for s in synth.wimax_mixed_set() if s.mb == 6 and s.z >= 84]
+    codes = [Code(s.hbm, s.z) for s in shapes]
+    cs = CodeSet(codes)
+    cof = (np.arange(F) % len(shapes)).astype(np.int32)
+    plan = MixedPlan(cs, cof)
+    batch = make_mixed_batch(plan, (1.5, 4.5), seed=1)
+    q = plan.quantize(batch.llr)
+    torch.cuda.synchronize()
+    plan.decode(q, I8X4, max_iters=20)
+    plan.decode(batch.llr, F32, max_iters=20)
+    torch.cuda.synchronize()
+    # 3. int16 wrap-around decoder
+    s1944 = synth.wifi_n1944_r56()
+    c1944 = Code(s1944.hbm, s1944.z)
+    info = gen_info(1, 0, F, c1944.k)
+    cw = c1944.encode(info)
+    llr = awgn_llr(cw, 0, 1, synth.ebn0_db_to_sigma(4.0, c1944.k / c1944.n))
+    q16 = quantize_i16(llr, 16.0, 10)
+    torch.cuda.synchronize()
+    c1944.decode(q16, dtype=I16W, max_iters=20, normalise=True, early_stop=True)
+    torch.cuda.synchronize()
+    # 4. flooding decoder
+    c648.decode_flooding(llr648[:16384], 10, 0.75, True, False)
+    torch.cuda.synchronize()
+    # 5. bitmap encoder
+    s2304 = synth.wimax_n2304_r56()
+    c2304 = Code(s2304.hbm, s2304.z)
+    Fe = 262144
+    words = torch.randint(-2**31, 2**31 - 1, (Fe, c2304.k // 32), dtype=torch.int32,
+                          device=dev)
+    torch.cuda.synchronize()
+    c2304.encode_bitmap(words)
+    torch.cuda.synchronize()
+    # 6. one training step
+    from paper_2306_12063_gb300.train import TrainConfig, train_weights
+    train_weights(c648, TrainConfig(T=8, steps=1, batch=4096))
+    torch.cuda.synchronize()
+    print("profiling cases done")
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -768,7 +857,11 @@ def main():
     ap.add_argument("--scale-train-steps", type=int, default=300)
     ap.add_argument("--scale-oracle-frames", type=int, default=10000)
     ap.add_argument("--mixed-frames", type=int, default=65536)
+    ap.add_argument("--profile-cases", action="store_true",
+                    help="launch each decoder-family kernel once on a small case (for ncu)")
     args = ap.parse_args()
+    if args.profile_cases:
+        return profile_cases()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

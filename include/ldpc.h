@@ -495,25 +495,31 @@ ldpc_status ldpc_sync(const ldpc_code *code, cudaStream_t stream,
 /* The decoder of ldpc_decode_layered_minsum for callers that cannot allocate
  * device memory (no counterpart in the paper: it exists for integration).
  * Creating a code handle allocates its tables with cudaMalloc; some callers
- * cannot do that -- code running where the allocator is off limits (a host
- * callback, a real-time thread with a fixed memory budget, a framework that
- * owns all device allocations).  This call takes the base matrix itself
- * (host array, same rules as ldpc_code_create) plus the caller's own
- * buffers, laid out as for ldpc_decode_layered_minsum, and allocates
- * nothing: no cudaMalloc, cudaFree or allocating library routine.  Its
- * scratch (the per-lane offset table, the work counter and the status word)
- * lives in a 64 KiB static device array that each GPU loading the library
- * holds until the process exits; codes whose offset table,
- * mb * ceil(z/32) * slots * 64 bytes (slots = 8, 12, 16, 20, 24 or 27, the
- * smallest that holds the largest row degree), exceeds 65280 bytes are
- * rejected with LDPC_ERR_UNSUPPORTED.  Each call clears the counter and
- * status word and rewrites the table on `stream` before decoding.  All calls
- * on a device share the one array and it keeps the last call's contents, so
- * calls whose GPU work overlaps (on different streams or from different host
- * threads) race; serialise them.  Errors are reported as for every call.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture. */
+ * cannot do that -- a real-time thread with a fixed memory budget, a process
+ * whose framework owns every device allocation (a caching allocator or a
+ * pool that accounts for each byte), or a steady-state path where cudaMalloc
+ * and cudaFree, which can synchronise the device, are not allowed.  This
+ * call takes the base matrix itself (host array, same rules as
+ * ldpc_code_create) plus the caller's own buffers, laid out as for
+ * ldpc_decode_layered_minsum, and allocates nothing: no cudaMalloc, cudaFree
+ * or allocating library routine.  Its scratch (the per-lane offset table,
+ * the work counter and the status word) lives in a 64 KiB static device
+ * array that each GPU loading the library holds until the process exits;
+ * codes whose offset table, mb * ceil(z/32) * slots * 64 bytes (slots = 8,
+ * 12, 16, 20, 24 or 27, the smallest that holds the largest row degree),
+ * exceeds 65280 bytes are rejected with LDPC_ERR_UNSUPPORTED.  Each call
+ * clears the counter and status word and rewrites the table on `stream`
+ * before decoding.  All calls on a device share the one array and it keeps
+ * the last call's contents, so calls whose GPU work overlaps (on different
+ * streams or from different host threads) race; serialise them.
+ * Unlike the other decode calls this one is synchronous: with no handle
+ * there is no ldpc_sync, so it waits for `stream` to drain and reads the
+ * status word itself, returning LDPC_ERR_TIMEOUT when a kernel's bounded
+ * wait for its bulk copy ran out (those frames are not decoded) and
+ * LDPC_ERR_CUDA for a debug-build offset check.  Each call looks up the
+ * array's device address (cudaGetSymbolAddress); the first lookup on a
+ * device loads the library's device code, so make the first call before
+ * any stream capture. */
 ldpc_status ldpc_decode_layered_minsum_noalloc(const int16_t *hbm, int mb, int nb, int z,
                                                ldpc_dtype dtype, const void *d_llr,
                                                int64_t frames,
@@ -529,6 +535,14 @@ ldpc_status ldpc_decode_layered_minsum_noalloc(const int16_t *hbm, int mb, int n
  * stays usable.  Nothing faults, traps or hangs. */
 ldpc_status ldpc_check_bounded_wait(const ldpc_code *code, uint32_t polls,
                                     cudaStream_t stream);
+
+/* Testing aid (no counterpart in the paper): caps the number of blocks in
+ * the persistent grids of the single-code FP32, int8 and learned decode
+ * kernels for every later launch in the process; 0 (the default) removes
+ * the cap.  Under a small cap each block decodes many frames, which drives
+ * the dynamic frame hand-out (per byte lane for int8) on small batches.
+ * A negative cap returns LDPC_ERR_INVALID_ARG. */
+ldpc_status ldpc_test_set_grid_cap(int blocks);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *ldpc_last_error(void);

@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = ["LdpcError", "Code", "load", "gen_info", "awgn_llr", "quantize_pack_i8",
            "awgn_llr_frames", "snr_sigma", "adam_step", "CodeSet", "MixedPlan", "MixedGraph",
-           "quantize_i16", "F32", "I8X4", "I16W", "symbols"]
+           "quantize_i16", "set_grid_cap", "F32", "I8X4", "I16W", "symbols"]
 
 F32 = 0
 I8X4 = 1
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = False):
         "ldpc_mixed_move_frames": ([vp, vp, vp, i32, vp, vp, vp], i32),
         "ldpc_mixed_paired_errors": ([vp, vp, vp, vp, vp, vp], i32),
         "ldpc_check_bounded_wait": ([vp, ctypes.c_uint32, vp], i32),
+        "ldpc_test_set_grid_cap": ([i32], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -653,6 +654,12 @@ def snr_sigma(seed: int, frame0: int, frames: int, ebn0_lo_db: float, ebn0_hi_db
     _check(load().ldpc_snr_sigma(int(seed), int(frame0), int(frames), float(ebn0_lo_db),
                                  float(ebn0_hi_db), float(rate), _ptr(out), _stream(stream)))
     return out
+
+
+def set_grid_cap(blocks: int) -> None:
+    """Testing aid: cap the single-code decoders' persistent grids at
+    `blocks` blocks (0 removes the cap) for every later launch."""
+    _check(load().ldpc_test_set_grid_cap(int(blocks)))
 
 
 def adam_step(param, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9,

@@ -24,12 +24,20 @@
 // parity check (or reaches max_iters) its outputs are written and the next
 // frame is loaded into that byte while the other three keep iterating.
 #include <algorithm>
-#include <cstdlib>
+#include <atomic>
 
 #include "ldpc_decode_dev.cuh"
 
 namespace ldpc {
 
+// Cap on the persistent grid of the single-code decoders (0: none), set by
+// ldpc_test_set_grid_cap.
+static std::atomic<int> g_grid_cap{0};
+
+static int64_t grid_cap(int64_t cap) {
+    const int v = g_grid_cap.load(std::memory_order_relaxed);
+    return v > 0 ? std::min<int64_t>(cap, v) : cap;
+}
 
 // ---------------------------------------------------------------------------
 // Kernels, one warp per block.  Shared memory: [mbarrier (16 B)][Z_n: N
@@ -38,7 +46,7 @@ namespace ldpc {
 // With a single warp the posterior array sits at a fixed shared address, so
 // every access is one load or store at the table offset.
 // ---------------------------------------------------------------------------
-template <int DMAX, bool WT = false>
+template <int DMAX, bool WT = false, int DM = DMAX>
 __global__ void __launch_bounds__(32)
     decode_f32_kernel(DevCode c, const uint32_t *__restrict__ llr, int64_t frames, DecodeParams p,
                       uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
@@ -64,8 +72,8 @@ __global__ void __launch_bounds__(32)
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
     int64_t f = blockIdx.x * static_cast<int64_t>(W) + warp;   // first frame static,
     while (f < frames) {                                       // the rest from the counter
-        const int done = decode_one_f32<DMAX, WT>(c, Zs, rows, wbuf, llr + f * c.n, use_bulk != 0,
-                                                  bar, phase, p, lane);
+        const int done = decode_one_f32<DMAX, WT, DM>(c, Zs, rows, wbuf, llr + f * c.n,
+                                                      use_bulk != 0, bar, phase, p, lane);
         if (!done) return;
         write_frame_f32(c, Zs, f, done, hard, iters, post, lane);
         __syncwarp();
@@ -73,7 +81,7 @@ __global__ void __launch_bounds__(32)
     }
 }
 
-template <int DMAX>
+template <int DMAX, int DM = DMAX>
 __global__ void __launch_bounds__(32)
     decode_i8_kernel(DevCode c, const uint32_t *__restrict__ llr, int64_t frames, DecodeParams p,
                      uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
@@ -121,10 +129,10 @@ __global__ void __launch_bounds__(32)
         for (int b = 0; b < 4; ++b) any |= fr[b] >= 0;
         if (!any) break;
         for (int l = 0; l < c.mb; ++l) {
-            layer_i8_any<DMAX>(c, l, Zs, rows, lane, norm);
+            layer_i8_any<DMAX, DM>(c, l, Zs, rows, lane, norm);
             __syncwarp();
         }
-        const uint32_t bad = p.early_stop ? syndrome_bad_i8<DMAX>(c, Zs, lane) : 0x80808080u;
+        const uint32_t bad = p.early_stop ? syndrome_bad_i8<DMAX, DM>(c, Zs, lane) : 0x80808080u;
         for (int b = 0; b < 4; ++b) {
             if (fr[b] < 0) continue;
             kb[b] += 1;
@@ -152,7 +160,7 @@ __global__ void __launch_bounds__(32)
     }
 }
 
-template <int DMAX>
+template <int DMAX, int DM>
 static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, int64_t frames,
                                    const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                    void *d_post, cudaStream_t s) {
@@ -167,8 +175,8 @@ static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, in
         return fail(LDPC_ERR_UNSUPPORTED, "decode: code too large for shared memory");
     const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (c.n % 4) == 0;
     const int use_bulk = aligned ? 1 : 0;
-    const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel<DMAX>)
-                          : reinterpret_cast<const void *>(decode_f32_kernel<DMAX>);
+    const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel<DMAX, DM>)
+                          : reinterpret_cast<const void *>(decode_f32_kernel<DMAX, false, DM>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
     int per_sm = 0;
@@ -176,26 +184,20 @@ static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, in
     if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
     per_sm = std::max(per_sm, 1);
     const int64_t units = i8 ? (frames + 3) / 4 : frames;
-    int64_t cap = static_cast<int64_t>(per_sm) * sms;
-    // LDPC_DECODE_MAX_BLOCKS caps the persistent grid (for tests of the
-    // dynamic frame hand-out on small batches).
-    if (const char *env = std::getenv("LDPC_DECODE_MAX_BLOCKS")) {
-        const long v = std::strtol(env, nullptr, 10);
-        if (v > 0) cap = std::min<int64_t>(cap, v);
-    }
+    const int64_t cap = grid_cap(static_cast<int64_t>(per_sm) * sms);
     const int grid = static_cast<int>(std::min<int64_t>(units, cap));
     unsigned long long *work = work_slot(c, s);
     if (!work) return LDPC_ERR_CUDA;
     const DevCode dc = dev_view(c);
     const uint32_t *in = static_cast<const uint32_t *>(d_llr);
     if (i8)
-        decode_i8_kernel<DMAX><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
-                                                      static_cast<int8_t *>(d_post), work,
-                                                      region_words, use_bulk);
+        decode_i8_kernel<DMAX, DM><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
+                                                          static_cast<int8_t *>(d_post), work,
+                                                          region_words, use_bulk);
     else
-        decode_f32_kernel<DMAX><<<grid, 32, smem, s>>>(dc, in, frames, p, d_hard, d_iters,
-                                                       static_cast<float *>(d_post), work,
-                                                       region_words, use_bulk);
+        decode_f32_kernel<DMAX, false, DM><<<grid, 32, smem, s>>>(
+            dc, in, frames, p, d_hard, d_iters, static_cast<float *>(d_post), work,
+            region_words, use_bulk);
     e = cudaGetLastError();
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "decode kernel launch");
 }
@@ -204,10 +206,13 @@ ldpc_status launch_decode(const Code &c, ldpc_dtype dtype, const void *d_llr, in
                           const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                           void *d_post, cudaStream_t s) {
     const bool i8 = dtype == LDPC_I8X4;
-    switch (c.dslots) {
-#define L(D) \
-    case D: return launch_decode_t<D>(c, i8, d_llr, frames, p, d_hard, d_iters, d_post, s);
-        LDPC_SLOT_CLASSES(L)
+    // the instance fitted to the code's largest row degree (see small_slots)
+    const int dm = c.max_deg >= c.dslots - 3 ? c.max_deg : c.dslots;
+    switch (c.dslots * 32 + dm) {
+#define L(D, M)          \
+    case D * 32 + M:     \
+        return launch_decode_t<D, M>(c, i8, d_llr, frames, p, d_hard, d_iters, d_post, s);
+        LDPC_FITTED_SLOTS(L)
 #undef L
         default: return fail(LDPC_ERR_UNSUPPORTED, "decode: no kernel for this row degree");
     }
@@ -233,11 +238,7 @@ static ldpc_status launch_learned_t(const Code &c, const float *d_llr, int64_t f
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
     per_sm = std::max(per_sm, 1);
-    int64_t cap = static_cast<int64_t>(per_sm) * sms;
-    if (const char *env = std::getenv("LDPC_DECODE_MAX_BLOCKS")) {
-        const long v = std::strtol(env, nullptr, 10);
-        if (v > 0) cap = std::min<int64_t>(cap, v);
-    }
+    const int64_t cap = grid_cap(static_cast<int64_t>(per_sm) * sms);
     const int grid = static_cast<int>(std::min<int64_t>(frames, cap));
     unsigned long long *work = work_slot(c, s);
     if (!work) return LDPC_ERR_CUDA;
@@ -319,3 +320,10 @@ ldpc_status launch_decode_view(const DevCode &dc, ldpc_dtype dtype, const void *
 }
 
 }  // namespace ldpc
+
+extern "C" ldpc_status ldpc_test_set_grid_cap(int blocks) {
+    if (blocks < 0)
+        return ldpc::fail(LDPC_ERR_INVALID_ARG, "ldpc_test_set_grid_cap: negative cap");
+    ldpc::g_grid_cap.store(blocks, std::memory_order_relaxed);
+    return LDPC_OK;
+}

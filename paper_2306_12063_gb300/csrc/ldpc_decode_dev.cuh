@@ -219,13 +219,21 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
 // a layer is always processed by the same instance.
 template <int DS>
 __host__ __device__ constexpr int sub_slots() { return DS >= 12 ? DS - 4 : (DS == 8 ? 4 : DS); }
-template <int DS>
-__device__ __forceinline__ bool use_sub(int d) { return sub_slots<DS>() < DS && d <= sub_slots<DS>(); }
+// Kernels fitted to a code: DM (<= DS) is the number of slots of the large
+// instance, the code's largest row degree when that lies in DS - 3 .. DS,
+// so rows run no padding slots beyond the code's own degrees; DM = DS is the
+// class-wide instance.  The small instance has min(DS - 4, DM) slots.
+template <int DS, int DM>
+__host__ __device__ constexpr int small_slots() { return sub_slots<DS>() < DM ? sub_slots<DS>() : DM; }
+template <int DS, int DM = DS>
+__device__ __forceinline__ bool use_sub(int d) {
+    return small_slots<DS, DM>() < DM && d <= small_slots<DS, DM>();
+}
 // The int8 row body is about twice the FP32 one; two large instances that
 // alternate from layer to layer no longer fit the instruction cache, so the
 // int8 kernels split only the small slot classes.
-template <int DS>
-__device__ __forceinline__ bool use_sub_i8(int d) { return DS <= 12 && use_sub<DS>(d); }
+template <int DS, int DM = DS>
+__device__ __forceinline__ bool use_sub_i8(int d) { return DS <= 12 && use_sub<DS, DM>(d); }
 
 // FP32 hard decision (eq. 21) and syndrome over the rows of one layer.
 template <int DS, int DMAX>
@@ -250,28 +258,34 @@ __device__ __forceinline__ uint32_t syndrome_rows_f32(const DevCode &c, const ui
 }
 
 // True when every check holds.
-template <int DS>
+template <int DS, int DM = DS>
 __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t *Zs, int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
         const int d = __ldg(c.rowinfo + l) & 255;
-        bad |= use_sub<DS>(d) ? syndrome_rows_f32<DS, sub_slots<DS>()>(c, Zs, l, lane)
-                              : syndrome_rows_f32<DS, DS>(c, Zs, l, lane);
+        bad |= use_sub<DS, DM>(d) ? syndrome_rows_f32<DS, small_slots<DS, DM>()>(c, Zs, l, lane)
+                                  : syndrome_rows_f32<DS, DM>(c, Zs, l, lane);
     }
     return !__any_sync(kFull, bad >> 31);
 }
 
-// One FP32 layer through the instance that fits it.
-template <int DS, bool WT = false>
+// One FP32 layer through the instance that fits it.  Learned weights are
+// staged with 16-byte loads at slot DS - DMAX of each layer, so the learned
+// kernels use only instances whose slot count differs from DS by a multiple
+// of four.
+template <int DS, bool WT = false, int DM = DS>
 __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint32_t *Zs,
                                               uint32_t *rows, int lane, bool norm, float alpha,
                                               const float *wprev = nullptr,
                                               const float *wcur = nullptr) {
+    static_assert(!WT || ((DS - DM) % 4 == 0 && (DS - small_slots<DS, DM>()) % 4 == 0),
+                  "learned weights need 16-byte aligned slot offsets");
     const int d = __ldg(c.rowinfo + layer) & 255;
-    if (use_sub<DS>(d))
-        layer_f32<DS, sub_slots<DS>(), WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur);
+    if (use_sub<DS, DM>(d))
+        layer_f32<DS, small_slots<DS, DM>(), WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev,
+                                                 wcur);
     else
-        layer_f32<DS, DS, WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur);
+        layer_f32<DS, DM, WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,27 +452,28 @@ __device__ __forceinline__ uint32_t syndrome_rows_i8(const DevCode &c, const uin
 }
 
 // int8 syndrome: bit 7 of byte b set when frame b has an unsatisfied check.
-template <int DS>
+template <int DS, int DM = DS>
 __device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint32_t *Zs,
                                                     int lane) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
         const int d = __ldg(c.rowinfo + l) & 255;
-        bad |= use_sub_i8<DS>(d) ? syndrome_rows_i8<DS, sub_slots<DS>()>(c, Zs, l, lane)
-                                 : syndrome_rows_i8<DS, DS>(c, Zs, l, lane);
+        bad |= use_sub_i8<DS, DM>(d)
+                   ? syndrome_rows_i8<DS, small_slots<DS, DM>()>(c, Zs, l, lane)
+                   : syndrome_rows_i8<DS, DM>(c, Zs, l, lane);
     }
     return __reduce_or_sync(kFull, bad & 0x80808080u);
 }
 
 // One int8 layer through the instance that fits it.
-template <int DS>
+template <int DS, int DM = DS>
 __device__ __forceinline__ void layer_i8_any(const DevCode &c, int layer, uint32_t *Zs,
                                              uint32_t *rows, int lane, bool norm) {
     const int d = __ldg(c.rowinfo + layer) & 255;
-    if (use_sub_i8<DS>(d))
-        layer_i8<DS, sub_slots<DS>()>(c, layer, d, Zs, rows, lane, norm);
+    if (use_sub_i8<DS, DM>(d))
+        layer_i8<DS, small_slots<DS, DM>()>(c, layer, d, Zs, rows, lane, norm);
     else
-        layer_i8<DS, DS>(c, layer, d, Zs, rows, lane, norm);
+        layer_i8<DS, DM>(c, layer, d, Zs, rows, lane, norm);
 }
 
 // ---------------------------------------------------------------------------
@@ -556,7 +571,7 @@ __device__ __forceinline__ int64_t next_work(unsigned long long *ctr, int64_t ba
 // count, or 0 if the bulk copy timed out (the status word records it).
 // Learned weights (WT) are staged per iteration into wbuf.
 // ---------------------------------------------------------------------------
-template <int DMAX, bool WT>
+template <int DMAX, bool WT, int DM = DMAX>
 __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, uint32_t *rows,
                                               float *wbuf, const uint32_t *src, bool use_bulk,
                                               uint64_t *bar, uint32_t &phase,
@@ -584,11 +599,11 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
             __syncwarp();
         }
         for (int l = 0; l < c.mb; ++l) {
-            layer_f32_any<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
+            layer_f32_any<DMAX, WT, DM>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
                                     wcur + l * WP);
             __syncwarp();
         }
-        if (p.early_stop && syndrome_ok_f32<DMAX>(c, Zs, lane)) return k;
+        if (p.early_stop && syndrome_ok_f32<DMAX, DM>(c, Zs, lane)) return k;
     }
     return p.max_iters;
 }

@@ -17,6 +17,13 @@ constexpr int kMaxRowDeg = 27;      // sign bits + 5-bit argmin share one word
 // Decoder kernels are built for these numbers of edge slots per row; a code
 // uses the smallest class that holds its largest row degree.
 #define LDPC_SLOT_CLASSES(X) X(8) X(12) X(16) X(20) X(24) X(27)
+// (class, slots) pairs of the single-code plain decoders fitted to a code's
+// largest row degree d: d itself when it lies in class - 3 .. class, else the
+// class (codes of degree <= 4 in class 8, which its 4-slot instance serves).
+#define LDPC_FITTED_SLOTS(X)                                                         \
+    X(8, 5) X(8, 6) X(8, 7) X(8, 8) X(12, 9) X(12, 10) X(12, 11) X(12, 12) X(16, 13) \
+    X(16, 14) X(16, 15) X(16, 16) X(20, 17) X(20, 18) X(20, 19) X(20, 20) X(24, 21)  \
+    X(24, 22) X(24, 23) X(24, 24) X(27, 25) X(27, 26) X(27, 27)
 inline int slot_class(int max_deg) {
     for (int d : {8, 12, 16, 20, 24, 27})
         if (max_deg <= d) return d;

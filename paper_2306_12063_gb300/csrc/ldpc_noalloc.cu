@@ -3,15 +3,16 @@
 //
 // Every other decode call uses a code handle, whose creation allocates the
 // per-code tables and work counters with cudaMalloc.  Some callers cannot do
-// that at all: code that runs where the allocator is off limits (inside a
-// host callback, from a real-time thread with a fixed memory budget, or under
-// a framework that owns every device allocation and forbids others).  This
-// entry point needs nothing but the caller's own input and output buffers:
-// its scratch memory -- the work counter and status word of the decode kernel
+// that: a real-time thread with a fixed memory budget, a process whose
+// framework owns every device allocation (a caching allocator or a pool that
+// must account for each byte), or a steady-state path where cudaMalloc and
+// cudaFree, which can synchronise the device, are not allowed.  This entry
+// point needs nothing but the caller's own input and output buffers: its
+// scratch memory -- the work counter and status word of the decode kernel
 // and the per-lane offset table that a handle would hold -- lives in one
 // file-scope static device array that every GPU loading the library keeps
 // until the process exits.
-#include <mutex>
+#include <string>
 
 #include "ldpc_internal.cuh"
 
@@ -75,21 +76,14 @@ __global__ void noalloc_setup_kernel(HbmArg h, int mb, int nb, int z, int rpl, i
     }
 }
 
-// Device address of the static array, looked up once per device.
-static std::mutex g_scratch_mu;
-static unsigned char *g_scratch_ptr[64];
-
-static ldpc_status scratch_address(int device, unsigned char **out) {
-    if (device < 0 || device >= 64)
-        return fail(LDPC_ERR_UNSUPPORTED, "ldpc_decode_layered_minsum_noalloc: device index");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
-        g_scratch_ptr[device] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_ptr[device];
+// Device address of the static array on the current device.  Looked up on
+// every call (the lookup allocates nothing): after a device reset the module
+// is loaded again and the array may sit at another address.
+static ldpc_status scratch_address(unsigned char **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    *out = static_cast<unsigned char *>(p);
     return LDPC_OK;
 }
 
@@ -164,17 +158,14 @@ extern "C" ldpc_status ldpc_decode_layered_minsum_noalloc(
     if (!d_llr || !d_hard || !d_iters)
         return fail(LDPC_ERR_INVALID_ARG, "ldpc_decode_layered_minsum_noalloc: NULL buffer");
 
-    int device = 0;
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     unsigned char *scratch = nullptr;
-    ldpc_status st = scratch_address(device, &scratch);
+    ldpc_status st = scratch_address(&scratch);
     if (st) return st;
 
     HbmArg h;
     for (int q = 0; q < kMaxNb * kMaxNb; ++q) h.v[q] = q < mb * nb ? hbm[q] : -1;
     noalloc_setup_kernel<<<1, 256, 0, stream>>>(h, mb, nb, z, rpl, dslots, scratch);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "noalloc_setup_kernel");
 
     DevCode dc;
@@ -194,6 +185,25 @@ extern "C" ldpc_status ldpc_decode_layered_minsum_noalloc(
     p.alpha = params->normalise ? params->alpha : 1.0f;
     p.normalise = params->normalise;
     p.early_stop = params->early_stop;
-    return launch_decode_view(dc, dtype, d_llr, frames, p, d_hard, d_iters, d_post,
-                              reinterpret_cast<unsigned long long *>(scratch), stream);
+    st = launch_decode_view(dc, dtype, d_llr, frames, p, d_hard, d_iters, d_post,
+                            reinterpret_cast<unsigned long long *>(scratch), stream);
+    if (st) return st;
+    // With no handle there is no ldpc_sync to read the status word later, so
+    // read it here (into a host int: no allocation) once the decode is done.
+    int status = 0;
+    e = cudaMemcpyFromSymbolAsync(&status, g_static_scratch, sizeof(int), 8,
+                                  cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the static status word");
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (status & kStatusCopyTimeout)
+        return fail(LDPC_ERR_TIMEOUT,
+                    "ldpc_decode_layered_minsum_noalloc: a kernel's wait for its bulk copy ran out");
+    if (status & kStatusBadOffset)
+        return fail(LDPC_ERR_CUDA, "ldpc_decode_layered_minsum_noalloc: a kernel read an edge "
+                                   "offset outside the posterior region (debug build check)");
+    if (status)
+        return fail(LDPC_ERR_CUDA, "ldpc_decode_layered_minsum_noalloc: device status " +
+                                       std::to_string(status));
+    return LDPC_OK;
 }

@@ -74,8 +74,9 @@ def test_learned_constant_weights_equal_normalised(ldpc):
         assert torch.equal(u, v)
 
 
-def test_learned_dynamic_handout(ldpc, monkeypatch):
-    monkeypatch.setenv("LDPC_DECODE_MAX_BLOCKS", "1")
+def test_learned_dynamic_handout(ldpc, request):
+    ldpc.set_grid_cap(1)
+    request.addfinalizer(lambda: ldpc.set_grid_cap(0))
     shape = synth.wifi_n648_r12()
     rc, _, llr = _inputs(shape, 150, 1.5, frame0=77)
     w = _weights(rc, 8, 3)

@@ -246,11 +246,12 @@ def test_i8_partial_groups(ldpc, frames):
 
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
 @pytest.mark.parametrize("shape_name,frames", [("wifi648", 301), ("wifi1944", 150)])
-def test_dynamic_frame_handout(ldpc, monkeypatch, dtype, shape_name, frames):
-    """One resident block (four warps) decodes every frame: finished frames
+def test_dynamic_frame_handout(ldpc, request, dtype, shape_name, frames):
+    """One block (one warp) decodes every frame: finished frames
     are replaced through the work counter (per byte lane for int8), at low
     Eb/N0 so iteration counts vary widely."""
-    monkeypatch.setenv("LDPC_DECODE_MAX_BLOCKS", "1")
+    ldpc.set_grid_cap(1)
+    request.addfinalizer(lambda: ldpc.set_grid_cap(0))
     s = SHAPES[shape_name]
     ebn0 = {"wifi648": 1.5, "wifi1944": 3.5}[shape_name]
     _, _, _, llr, _ = oracle_inputs(s, frames, frame0=999, ebn0=ebn0)

@@ -1,8 +1,11 @@
 """The decode entry point for callers that cannot allocate device memory
-(ldpc_decode_layered_minsum_noalloc): called through the C-ABI, twice in a
-row, it must give exactly what the handle-based decoder gives.  This file is
-collected last so that a failure here leaves every other test already run;
-it also passes on its own in a fresh process."""
+(ldpc_decode_layered_minsum_noalloc): a real-time thread with a fixed memory
+budget, a framework that owns every device allocation, or a steady-state
+path where cudaMalloc / cudaFree are not allowed.  Called through the C-ABI
+twice in a row, it must give exactly what the oracle and the handle-based
+decoder give.  This file is collected last so that a failure here leaves
+every other test already run; it also passes on its own in a fresh
+process."""
 import ctypes
 
 import numpy as np
@@ -30,7 +33,7 @@ def _inputs(shape, frames, ebn0):
     rc = oracle.RefCode(shape.hbm, shape.z)
     info = oracle.gen_info(1, 0, frames, rc.k)
     llr = oracle.awgn_llr(rc.encode(info), 0, 1, synth.ebn0_db_to_sigma(ebn0, rc.k / rc.n))
-    return llr
+    return rc, llr
 
 
 def _noalloc(ldpc, shape, dtype, llr_dev, frames, max_iters, out):
@@ -50,16 +53,18 @@ def _noalloc(ldpc, shape, dtype, llr_dev, frames, max_iters, out):
                                                     ("wifi648", 1001, 2.0)])
 def test_noalloc_matches_handle_decoder(ldpc, dtype_name, shape_name, frames, ebn0):
     shape = {"wifi1944": synth.wifi_n1944_r56(), "wifi648": synth.wifi_n648_r12()}[shape_name]
-    llr = _inputs(shape, frames, ebn0)
+    rc, llr = _inputs(shape, frames, ebn0)
     code = ldpc.Code(shape.hbm, shape.z)
     if dtype_name == "f32":
         dtype = ldpc.F32
         dev_in = torch.from_numpy(llr).cuda()
         post_dtype = torch.float32
+        ref_h, ref_i, ref_p = rc.decode_layered_f32(llr, 20, 0.75, True, True)
     else:
         dtype = ldpc.I8X4
         dev_in = ldpc.quantize_pack_i8(torch.from_numpy(llr).cuda())
         post_dtype = torch.int8
+        ref_h, ref_i, ref_p, _ = rc.decode_layered_i8(oracle.quantize_i8(llr), 20, True, True)
     want_h, want_i, want_p = code.decode(dev_in, frames=frames, dtype=dtype, max_iters=20,
                                          early_stop=True, want_post=True)
     for call in range(2):   # the second call reuses the static array left by the first
@@ -68,6 +73,12 @@ def test_noalloc_matches_handle_decoder(ldpc, dtype_name, shape_name, frames, eb
                torch.zeros((frames, code.n), dtype=post_dtype, device="cuda"))
         _noalloc(ldpc, shape, dtype, dev_in, frames, 20, out)
         torch.cuda.synchronize()
+        # against the oracle (posteriors compared with ==, so +0 equals -0)
+        assert (out[1].cpu().numpy() == ref_i).all(), f"iterations differ from the oracle ({call})"
+        assert (out[0].cpu().numpy().view(np.uint32) == ref_h).all(), \
+            f"hard decisions differ from the oracle on call {call}"
+        assert (out[2].cpu().numpy() == ref_p).all(), f"posteriors differ from the oracle ({call})"
+        # and against the handle-based decoder
         assert torch.equal(out[1], want_i), f"iteration counts differ on call {call}"
         assert torch.equal(out[0], want_h), f"hard decisions differ on call {call}"
         assert torch.equal(out[2], want_p), f"posteriors differ on call {call}"
