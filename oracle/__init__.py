@@ -88,6 +88,8 @@ def lib():
                                              ctypes.POINTER(_Params), vp, vp, vp]
             L.ldpc_ref_decode_layered_weighted_f32.argtypes = [vp, vp, i64, vp, i32, i32,
                                                                vp, vp, vp]
+            L.ldpc_ref_decode_learned_f32.argtypes = [vp, vp, i64, vp, i32, i32, i32, vp, vp,
+                                                      vp, vp, vp]
             L.ldpc_ref_decode_layered_i8.argtypes = [
                 vp, vp, i64, ctypes.POINTER(_Params), vp, vp, vp,
                 ctypes.POINTER(i64)]
@@ -185,6 +187,23 @@ class RefCode:
         _check(lib().ldpc_ref_decode_layered_weighted_f32(
             self._h, _ptr(llr), F, _ptr(w), T, int(early_stop), _ptr(hard), _ptr(iters),
             _ptr(post)), "ldpc_ref_decode_layered_weighted_f32")
+        return hard, iters, post
+
+    def decode_learned_f32(self, llr, weights, max_iters=None, early_stop=True,
+                           stop_iter=(0, 0), stop_frac=(0.0, 0.0), want_post=True):
+        """Learned normalised min-sum run for up to max_iters iterations
+        (rows past the table's T repeat its last row), with give-up
+        checkpoints (stop_iter[j], stop_frac[j]); see ldpc_oracle.h."""
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        T = w.shape[0]
+        max_iters = T if max_iters is None else int(max_iters)
+        si = np.ascontiguousarray(stop_iter, dtype=np.int32)
+        sf = np.ascontiguousarray(stop_frac, dtype=np.float32)
+        llr, F, hard, iters, post, _ = self._decode(
+            None, llr, np.float32, max_iters, 1.0, False, early_stop, want_post, np.float32)
+        _check(lib().ldpc_ref_decode_learned_f32(
+            self._h, _ptr(llr), F, _ptr(w), T, max_iters, int(early_stop), _ptr(si), _ptr(sf),
+            _ptr(hard), _ptr(iters), _ptr(post)), "ldpc_ref_decode_learned_f32")
         return hard, iters, post
 
     def decode_flooding_f32(self, llr, max_iters=10, alpha=0.75, normalise=True,

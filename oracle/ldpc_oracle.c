@@ -806,14 +806,30 @@ static int block_edge_base(const ldpc_ref_code *c, int i) {
     return q;
 }
 
-int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *llr,
-                                         int64_t frames, const float *weights, int T,
-                                         int early_stop, uint32_t *hard, int32_t *iters,
-                                         float *post) {
-    ldpc_ref_params p = {T, 1.0f, 0, early_stop};
+/* Give-up checkpoint j (0 when there is none). */
+static int stop_iter_of(const int *stop_iter, int j) { return stop_iter ? stop_iter[j] : 0; }
+
+/* Learned normalised min-sum (see the header).  The weights of iteration k
+ * are row min(k, T) - 1 of the table, so iterations past T repeat the last
+ * row.  After each iteration with early_stop the unsatisfied checks u of the
+ * hard decisions are counted: u = 0 stops the frame (eq. 21, Section 4
+ * step 4); so does u > floor(stop_frac[j] * M) at iteration stop_iter[j]
+ * (the give-up rule for frames the decoder is not converging on). */
+int ldpc_ref_decode_learned_f32(const ldpc_ref_code *c, const float *llr, int64_t frames,
+                                const float *weights, int T, int max_iters, int early_stop,
+                                const int *stop_iter, const float *stop_frac, uint32_t *hard,
+                                int32_t *iters, float *post) {
+    ldpc_ref_params p = {max_iters, 1.0f, 0, early_stop};
     int st = check_params(c, &p, frames, llr, hard, iters);
     if (st) return st;
-    if (!weights && frames) return LDPC_REF_ERR_INVALID_ARG;
+    if ((!weights && frames) || T < 1) return LDPC_REF_ERR_INVALID_ARG;
+    int limit[2] = {-1, -1};
+    for (int j = 0; j < 2; j++) {
+        if (!stop_iter || stop_iter[j] == 0) continue;
+        if (stop_iter[j] < 1 || !early_stop || !(stop_frac[j] >= 0.0f))
+            return LDPC_REF_ERR_INVALID_ARG;
+        limit[j] = (int)floorf(stop_frac[j] * (float)c->m);
+    }
     const int n = c->n, nw = (n + 31) / 32;
     int nnzb = 0;
     for (int q = 0; q < c->mb * c->nb; q++) nnzb += c->hbm[q] >= 0;
@@ -829,9 +845,10 @@ int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *ll
     for (int64_t f = 0; f < frames; f++) {
         for (int v = 0; v < n; v++) Zn[v] = llr[f * (int64_t)n + v];
         for (int e = 0; e < c->nnz; e++) L[e] = 0.0f;
-        int done = T;
-        for (int k = 1; k <= T; k++) {
-            const float *wk = weights + (size_t)(k - 1) * nnzb;
+        int done = max_iters;
+        for (int k = 1; k <= max_iters; k++) {
+            const int row_w = (k < T ? k : T) - 1;
+            const float *wk = weights + (size_t)row_w * nnzb;
             for (int i = 0; i < c->mb; i++) {
                 const int q0 = block_edge_base(c, i);
                 for (int r = 0; r < c->z; r++) {
@@ -850,7 +867,12 @@ int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *ll
             }
             if (early_stop) {
                 hard_from_f32(Zn, n, hard + f * (int64_t)nw, bits);
-                if (ldpc_ref_syndrome_weight(c, bits) == 0) { done = k; break; }
+                const int u = ldpc_ref_syndrome_weight(c, bits);
+                if (u == 0 || (k == stop_iter_of(stop_iter, 0) && u > limit[0]) ||
+                    (k == stop_iter_of(stop_iter, 1) && u > limit[1])) {
+                    done = k;
+                    break;
+                }
             }
         }
         hard_from_f32(Zn, n, hard + f * (int64_t)nw, bits);
@@ -859,4 +881,12 @@ int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *ll
     }
     free(Zn); free(L); free(Q); free(Ln); free(bits);
     return LDPC_REF_OK;
+}
+
+int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *llr,
+                                         int64_t frames, const float *weights, int T,
+                                         int early_stop, uint32_t *hard, int32_t *iters,
+                                         float *post) {
+    return ldpc_ref_decode_learned_f32(c, llr, frames, weights, T, T, early_stop, NULL, NULL,
+                                       hard, iters, post);
 }
