@@ -188,6 +188,30 @@ ldpc_status ldpc_decode_learned_minsum(const ldpc_code *code, const float *d_llr
                                        int early_stop, uint32_t *d_hard, int32_t *d_iters,
                                        float *d_post, cudaStream_t stream);
 
+/* Run limits of the learned decoder beyond the weight table and a give-up
+ * rule (extensions; the paper has neither).  Iteration k uses weight row
+ * min(k, T) - 1, so iterations past the table's T rows repeat its last row.
+ * With early_stop the unsatisfied checks u of the hard decisions are counted
+ * after every iteration; a frame stops when u = 0 (eq. 21) or when k equals
+ * stop_iter[j] (j = 0, 1; 0 = no checkpoint) and u > floor(stop_frac[j] * M),
+ * the product rounded in FP32: a frame still far from a codeword there is
+ * given up (its outputs are those of iteration k, its count k).
+ * Checkpoints need early_stop = 1; stop_frac must be >= 0. */
+typedef struct {
+    int max_iters;       /* 1..1000 iterations at most; 0 = T (the table's rows) */
+    int early_stop;      /* 0 or 1 */
+    int stop_iter[2];    /* give-up checkpoints, 0..1000 (0 = none) */
+    float stop_frac[2];  /* their limits as fractions of M */
+} ldpc_learned_params;
+
+/* ldpc_decode_learned_minsum with the run limits above (lp->max_iters may
+ * exceed T).  With max_iters = T and no checkpoints it is
+ * ldpc_decode_learned_minsum. */
+ldpc_status ldpc_decode_learned_minsum_ex(const ldpc_code *code, const float *d_llr,
+                                          int64_t frames, const float *d_weights, int T,
+                                          const ldpc_learned_params *lp, uint32_t *d_hard,
+                                          int32_t *d_iters, float *d_post, cudaStream_t stream);
+
 /* Flooding min-sum (Section 4, eq. 18-21) in FP32, the schedule the layered
  * decoder improves on: each iteration first computes every check message
  * from the previous iteration's messages, Z_mn = Z_n^(0) + sum over the
@@ -409,6 +433,14 @@ ldpc_status ldpc_mixed_set_weights(ldpc_mixed_plan *plan, const float *const *h_
 ldpc_status ldpc_decode_mixed_learned(ldpc_mixed_plan *plan, const float *d_llr, int early_stop,
                                       uint32_t *d_hard, int32_t *d_iters, float *d_post,
                                       cudaStream_t stream);
+
+/* ldpc_decode_mixed_learned with the run limits of ldpc_learned_params
+ * (lp->max_iters = 0: T_c per code; otherwise every code runs up to
+ * lp->max_iters iterations, rows past T_c repeating its last row; the
+ * give-up limits are fractions of each code's M). */
+ldpc_status ldpc_decode_mixed_learned_ex(ldpc_mixed_plan *plan, const float *d_llr,
+                                         const ldpc_learned_params *lp, uint32_t *d_hard,
+                                         int32_t *d_iters, float *d_post, cudaStream_t stream);
 
 /* d_bad uint8[frames]: 1 where a frame's hard decisions (plan layout)
  * violate a parity check (eq. 21 termination test), else 0. */

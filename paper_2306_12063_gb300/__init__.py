@@ -39,6 +39,21 @@ class _Params(ctypes.Structure):
                 ("normalise", ctypes.c_int), ("early_stop", ctypes.c_int)]
 
 
+class _LearnedParams(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("early_stop", ctypes.c_int),
+                ("stop_iter", ctypes.c_int * 2), ("stop_frac", ctypes.c_float * 2)]
+
+
+def _learned_params(max_iters, early_stop, stop_iter, stop_frac):
+    lp = _LearnedParams()
+    lp.max_iters = int(max_iters or 0)
+    lp.early_stop = int(bool(early_stop))
+    for j in range(2):
+        lp.stop_iter[j] = int(stop_iter[j])
+        lp.stop_frac[j] = float(stop_frac[j])
+    return lp
+
+
 _lib = None
 
 
@@ -82,6 +97,9 @@ def load(build_if_missing: bool = False):
         "ldpc_decode_layered_minsum_noalloc": ([vp, i32, i32, i32, i32, vp, i64, P(_Params),
                                                 vp, vp, vp, vp], i32),
         "ldpc_decode_learned_minsum": ([vp, vp, i64, vp, i32, i32, vp, vp, vp, vp], i32),
+        "ldpc_decode_learned_minsum_ex": ([vp, vp, i64, vp, i32, P(_LearnedParams), vp, vp, vp,
+                                           vp], i32),
+        "ldpc_decode_mixed_learned_ex": ([vp, vp, P(_LearnedParams), vp, vp, vp, vp], i32),
         "ldpc_learned_fallback_workspace_bytes": ([vp, i64], sz),
         "ldpc_decode_learned_fallback": ([vp, vp, i64, vp, i32, P(_Params), f32, i32, vp, vp,
                                           P(i64), vp, sz, vp], i32),
@@ -254,8 +272,12 @@ class Code:
         return int((self.hbm >= 0).sum())
 
     def decode_learned(self, llr, weights, early_stop: bool = True, want_post: bool = False,
-                       out=None, stream=None):
-        """Learned normalised min-sum: weights float32[T][nnz_blocks] on the GPU."""
+                       out=None, stream=None, max_iters: Optional[int] = None,
+                       stop_iter=(0, 0), stop_frac=(0.0, 0.0)):
+        """Learned normalised min-sum: weights float32[T][nnz_blocks] on the GPU.
+        max_iters (default T) may exceed T: later iterations repeat the last
+        weight row; (stop_iter[j], stop_frac[j]) are give-up checkpoints
+        (ldpc_learned_params)."""
         torch = _torch()
         F, T = llr.shape[0], weights.shape[0]
         if out is None:
@@ -265,9 +287,16 @@ class Code:
                     if want_post else None)
         else:
             hard, iters, post = out
-        _check(load().ldpc_decode_learned_minsum(self._h, _ptr(llr), int(F), _ptr(weights),
-                                                 int(T), int(bool(early_stop)), _ptr(hard),
-                                                 _ptr(iters), _ptr(post), _stream(stream)))
+        if max_iters is None and not any(stop_iter):
+            _check(load().ldpc_decode_learned_minsum(self._h, _ptr(llr), int(F), _ptr(weights),
+                                                     int(T), int(bool(early_stop)), _ptr(hard),
+                                                     _ptr(iters), _ptr(post), _stream(stream)))
+        else:
+            lp = _learned_params(max_iters, early_stop, stop_iter, stop_frac)
+            _check(load().ldpc_decode_learned_minsum_ex(self._h, _ptr(llr), int(F),
+                                                        _ptr(weights), int(T), ctypes.byref(lp),
+                                                        _ptr(hard), _ptr(iters), _ptr(post),
+                                                        _stream(stream)))
         return hard, iters, post
 
     def learned_workspace_bytes(self, frames: int) -> int:
@@ -516,7 +545,11 @@ class MixedPlan:
         _check(load().ldpc_mixed_set_weights(self._h, ptrs, T.ctypes.data_as(ctypes.c_void_p)))
 
     def decode_learned(self, llr, early_stop: bool = True, want_post: bool = False, out=None,
-                       stream=None):
+                       stream=None, max_iters: int = 0, stop_iter=(0, 0),
+                       stop_frac=(0.0, 0.0)):
+        """Learned decoding of every frame with its code's weights; max_iters
+        0 runs T_c iterations per code, more repeat each table's last row;
+        (stop_iter[j], stop_frac[j]) are give-up checkpoints."""
         torch = _torch()
         if out is None:
             hard, iters = self.empty_outputs()
@@ -524,9 +557,15 @@ class MixedPlan:
                     if want_post else None)
         else:
             hard, iters, post = out
-        _check(load().ldpc_decode_mixed_learned(self._h, _ptr(llr), int(bool(early_stop)),
-                                                _ptr(hard), _ptr(iters), _ptr(post),
-                                                _stream(stream)))
+        if not max_iters and not any(stop_iter):
+            _check(load().ldpc_decode_mixed_learned(self._h, _ptr(llr), int(bool(early_stop)),
+                                                    _ptr(hard), _ptr(iters), _ptr(post),
+                                                    _stream(stream)))
+        else:
+            lp = _learned_params(max_iters, early_stop, stop_iter, stop_frac)
+            _check(load().ldpc_decode_mixed_learned_ex(self._h, _ptr(llr), ctypes.byref(lp),
+                                                       _ptr(hard), _ptr(iters), _ptr(post),
+                                                       _stream(stream)))
         return hard, iters, post
 
     def frame_flags(self, hard, out=None, stream=None):

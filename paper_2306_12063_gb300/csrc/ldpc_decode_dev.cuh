@@ -235,6 +235,24 @@ __device__ __forceinline__ bool use_sub(int d) {
 template <int DS, int DM = DS>
 __device__ __forceinline__ bool use_sub_i8(int d) { return DS <= 12 && use_sub<DS, DM>(d); }
 
+// FP32 hard decision (eq. 21) and parity of row slot t of layer l: bit 31
+// set when the check is unsatisfied.
+template <int DS, int DMAX>
+__device__ __forceinline__ uint32_t syndrome_row_f32(const DevCode &c, const uint32_t *Zs, int l,
+                                                     int t, int lane) {
+    const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
+    uint32_t off[DMAX];
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
+    uint32_t par = 0;
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) {
+        const uint32_t u = lds_u32(Zs, off[i]);
+        par ^= (u - 1u) | u;   // bit 31 set iff Z <= 0 (negatives, -0 and +0)
+    }
+    return par;
+}
+
 // FP32 hard decision (eq. 21) and syndrome over the rows of one layer.
 template <int DS, int DMAX>
 __device__ __forceinline__ uint32_t syndrome_rows_f32(const DevCode &c, const uint32_t *Zs, int l,
@@ -242,19 +260,29 @@ __device__ __forceinline__ uint32_t syndrome_rows_f32(const DevCode &c, const ui
     uint32_t bad = 0;
     for (int t = 0; t < c.rpl; ++t) {
         if (lane + 32 * t >= c.z) break;
-        const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DS * 32) + (DS - DMAX) * 32 + lane;
-        uint32_t off[DMAX];
-#pragma unroll
-        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
-        uint32_t par = 0;
-#pragma unroll
-        for (int i = 0; i < DMAX; ++i) {
-            const uint32_t u = lds_u32(Zs, off[i]);
-            par ^= (u - 1u) | u;   // bit 31 set iff Z <= 0 (negatives, -0 and +0)
-        }
-        bad |= par;
+        bad |= syndrome_row_f32<DS, DMAX>(c, Zs, l, t, lane);
     }
     return bad;
+}
+
+// Unsatisfied checks of the hard decisions (eq. 21), warp-uniform.
+template <int DS, int DM = DS>
+__device__ __forceinline__ int syndrome_count_f32(const DevCode &c, const uint32_t *Zs,
+                                                  int lane) {
+    uint32_t cnt = 0;
+    for (int l = 0; l < c.mb; ++l) {
+        const int d = __ldg(c.rowinfo + l) & 255;
+        if (use_sub<DS, DM>(d)) {
+            for (int t = 0; t < c.rpl; ++t)
+                if (lane + 32 * t < c.z)
+                    cnt += syndrome_row_f32<DS, small_slots<DS, DM>()>(c, Zs, l, t, lane) >> 31;
+        } else {
+            for (int t = 0; t < c.rpl; ++t)
+                if (lane + 32 * t < c.z)
+                    cnt += syndrome_row_f32<DS, DM>(c, Zs, l, t, lane) >> 31;
+        }
+    }
+    return static_cast<int>(__reduce_add_sync(kFull, cnt));
 }
 
 // True when every check holds.
@@ -584,14 +612,21 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
     for (int i = lane; i < c.m * kRowWordsF32; i += 32) rows[i] = 0u;   // all L_mn = 0
     __syncwarp();
     const bool norm = p.normalise != 0;
+    const int wT = p.weight_iters > 0 ? p.weight_iters : p.max_iters;
+    const bool checkpoints = p.early_stop && (p.stop_iter[0] | p.stop_iter[1]) != 0;
+    // give-up limits, floor(stop_frac * M) with the product rounded in FP32
+    const int lim0 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[0], static_cast<float>(c.m))));
+    const int lim1 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[1], static_cast<float>(c.m))));
     for (int k = 1; k <= p.max_iters; ++k) {
         constexpr int WP = wpad(DMAX);
         float *wcur = wbuf + (k & 1) * c.mb * WP;
         const float *wprev = k > 1 ? wbuf + ((k - 1) & 1) * c.mb * WP : wcur;
-        if (WT) {
-            // stage w[k-1] in slot order; iteration 1 also serves as its own
-            // "previous" weights (they multiply zero messages)
-            const float *wk = p.weights + static_cast<size_t>(k - 1) * p.n_edges;
+        if (WT && k <= wT + 1) {
+            // stage the weights of iteration k (row min(k, T) - 1) in slot
+            // order; iteration 1 also serves as its own "previous" weights
+            // (they multiply zero messages).  From iteration T + 2 on both
+            // buffers already hold row T - 1.
+            const float *wk = p.weights + static_cast<size_t>(min(k, wT) - 1) * p.n_edges;
             for (int i = lane; i < c.mb * WP; i += 32) {
                 const int g = __ldg(c.wgather + i);
                 wcur[i] = g >= 0 ? __ldg(wk + g) : 0.0f;
@@ -603,7 +638,15 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
                                     wcur + l * WP);
             __syncwarp();
         }
-        if (p.early_stop && syndrome_ok_f32<DMAX, DM>(c, Zs, lane)) return k;
+        if (checkpoints) {
+            // count the unsatisfied checks: none ends the frame (eq. 21), too
+            // many at a give-up checkpoint ends it too
+            const int u = syndrome_count_f32<DMAX, DM>(c, Zs, lane);
+            if (u == 0 || (k == p.stop_iter[0] && u > lim0) || (k == p.stop_iter[1] && u > lim1))
+                return k;
+        } else if (p.early_stop && syndrome_ok_f32<DMAX, DM>(c, Zs, lane)) {
+            return k;
+        }
     }
     return p.max_iters;
 }

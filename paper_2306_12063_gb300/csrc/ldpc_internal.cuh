@@ -110,10 +110,17 @@ struct DecodeParams {
     float alpha;
     int normalise;
     int early_stop;
-    // learned normalised min-sum (FP32 only): weights[T][n_edges], T = max_iters;
-    // NULL for the plain / alpha-scaled decoder
+    // learned normalised min-sum (FP32 only): weights[T][n_edges], NULL for
+    // the plain / alpha-scaled decoder; T = weight_iters (0: max_iters), and
+    // iterations past T use row T - 1
     const float *weights = nullptr;
     int n_edges = 0;
+    int weight_iters = 0;
+    // give-up checkpoints (0: none; need early_stop): at iteration
+    // stop_iter[j] a frame with more than floor(stop_frac[j] * M) unsatisfied
+    // checks stops
+    int stop_iter[2] = {0, 0};
+    float stop_frac[2] = {0.0f, 0.0f};
 };
 
 // Launchers (defined in the .cu files).
@@ -162,6 +169,10 @@ ldpc_status learned_fallback(const Code &c, const float *d_llr, int64_t frames,
                              const DecodeParams &learned, const DecodeParams &fb, float scale,
                              int clip, uint32_t *d_hard, int32_t *d_iters, int64_t *h_count,
                              void *d_ws, cudaStream_t s);
+
+// Validates the learned decoder's run limits and copies them into dp
+// (max_iters 0 means "the weight table's T").
+ldpc_status learned_run_params(const ldpc_learned_params *lp, DecodeParams *dp, const char *who);
 
 // Decode launch on a caller-assembled code view (tables, status word and work
 // counter supplied by the caller); no allocation.

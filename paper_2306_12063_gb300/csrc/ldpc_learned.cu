@@ -178,11 +178,58 @@ static ldpc_status learned_params(const ldpc_code *code, int64_t frames, const f
     return LDPC_OK;
 }
 
+ldpc_status learned_run_params(const ldpc_learned_params *lp, DecodeParams *dp, const char *who) {
+    if (!lp) return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": run limits are NULL");
+    if (lp->max_iters < 0 || lp->max_iters > kMaxIters)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": max_iters outside 0..1000");
+    if (lp->early_stop != 0 && lp->early_stop != 1)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": early_stop must be 0 or 1");
+    for (int j = 0; j < 2; ++j) {
+        if (lp->stop_iter[j] < 0 || lp->stop_iter[j] > kMaxIters)
+            return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": stop_iter outside 0..1000");
+        if (lp->stop_iter[j] && (!lp->early_stop || !(lp->stop_frac[j] >= 0.0f) ||
+                                 !(lp->stop_frac[j] <= 1e6f)))
+            return fail(LDPC_ERR_INVALID_ARG,
+                        std::string(who) + ": a checkpoint needs early_stop and stop_frac >= 0");
+    }
+    dp->max_iters = lp->max_iters;
+    dp->alpha = 1.0f;
+    dp->normalise = 0;
+    dp->early_stop = lp->early_stop;
+    for (int j = 0; j < 2; ++j) {
+        dp->stop_iter[j] = lp->stop_iter[j];
+        dp->stop_frac[j] = lp->stop_iter[j] ? lp->stop_frac[j] : 0.0f;
+    }
+    return LDPC_OK;
+}
+
 }  // namespace ldpc
 
 using namespace ldpc;
 
 extern "C" {
+
+ldpc_status ldpc_decode_learned_minsum_ex(const ldpc_code *code, const float *d_llr,
+                                          int64_t frames, const float *d_weights, int T,
+                                          const ldpc_learned_params *lp, uint32_t *d_hard,
+                                          int32_t *d_iters, float *d_post, cudaStream_t stream) {
+    const char *who = "ldpc_decode_learned_minsum_ex";
+    DecodeParams p;
+    ldpc_status st = learned_params(code, frames, d_weights, T, 0, &p, who);
+    if (st) return st;
+    st = learned_run_params(lp, &p, who);
+    if (st) return st;
+    p.weights = d_weights;
+    p.n_edges = code->c.n_edges;
+    p.weight_iters = T;
+    if (p.max_iters == 0) p.max_iters = T;
+    if (frames == 0) return LDPC_OK;
+    if (!d_llr || !d_hard || !d_iters)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": NULL buffer");
+    cudaError_t e = cudaSetDevice(code->c.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return launch_decode_learned(code->c, d_llr, frames, p, d_hard, d_iters, d_post, stream);
+}
 
 ldpc_status ldpc_decode_learned_minsum(const ldpc_code *code, const float *d_llr, int64_t frames,
                                        const float *d_weights, int T, int early_stop,

@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(32)
         DecodeParams pc = p;
         if (WT) {
             pc.weights = wptr[item.code];
-            pc.max_iters = wT[item.code];
+            pc.weight_iters = wT[item.code];
+            pc.max_iters = p.max_iters > 0 ? p.max_iters : wT[item.code];
             pc.n_edges = c.n_edges;
         }
         Zs[c.n + lane] = 0x7F800000u;   // dummy posterior of unused edge slots
@@ -1202,10 +1203,29 @@ ldpc_status ldpc_decode_mixed_learned(ldpc_mixed_plan *plan, const float *d_llr,
     ldpc_status st = bind_plan(p);
     if (st != LDPC_OK) return st;
     DecodeParams dp;
-    dp.max_iters = 1;   // per code from the weight table
+    dp.max_iters = 0;   // per code: T_c of its weight table
     dp.alpha = 1.0f;
     dp.normalise = 0;
     dp.early_stop = early_stop;
+    return launch_all(p, 2, d_llr, dp, d_hard, d_iters, d_post, stream);
+}
+
+ldpc_status ldpc_decode_mixed_learned_ex(ldpc_mixed_plan *plan, const float *d_llr,
+                                         const ldpc_learned_params *lp, uint32_t *d_hard,
+                                         int32_t *d_iters, float *d_post, cudaStream_t stream) {
+    const char *who = "ldpc_decode_mixed_learned_ex";
+    if (!plan || !lp) return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": NULL argument");
+    DecodeParams dp;
+    ldpc_status st = learned_run_params(lp, &dp, who);
+    if (st) return st;
+    MixedPlan &p = *plan->p;
+    if (p.frames == 0) return LDPC_OK;
+    if (!p.d_wptr)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": no weights (ldpc_mixed_set_weights)");
+    if (!d_llr || !d_hard || !d_iters)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": NULL buffer");
+    st = bind_plan(p);
+    if (st != LDPC_OK) return st;
     return launch_all(p, 2, d_llr, dp, d_hard, d_iters, d_post, stream);
 }
 

@@ -147,6 +147,36 @@ def train_weights(code: Code, cfg: TrainConfig = TrainConfig(), weights=None,
     return TrainResult(weights, hist, cfg, m, v, max(s1, s0))
 
 
+def operating_range(code: Code, lo: float = 1.5, hi: float = 4.5, step: float = 0.25,
+                    frames: int = 4096, fer_max: float = 0.5, max_iters: int = 20,
+                    alpha: float = 0.75, seed: int = 7, stream=None) -> Tuple[float, float]:
+    """Eb/N0 training range of a code where plain min-sum decodes it (a
+    reading of the training recipe for codes of many rates): the lowest
+    step b = lo, lo + step, ... whose centre b + step / 2 gives a frame-error
+    rate of at most fer_max for plain FP32 layered min-sum (alpha, max_iters
+    iterations, early stop) on `frames` calibration frames of their own seed,
+    and the range [b, max(b + 1, hi)] dB.  Every decode and count runs in the
+    library's kernels."""
+    from . import awgn_llr
+    dev = code.device
+    rate = code.k / code.n
+    info = gen_info(seed, 0, frames, code.k, device=dev, stream=stream)
+    cw = code.encode(info, stream=stream)
+    b = lo
+    nsteps = int(round((hi - lo) / step))
+    for i in range(nsteps):
+        b = lo + i * step
+        # unit-energy BPSK: sigma^2 = 1 / (2 R 10^(Eb/N0 / 10))
+        sigma = (1.0 / (2.0 * rate * 10.0 ** ((b + step / 2) / 10.0))) ** 0.5
+        llr = awgn_llr(cw, 0, seed + 1 + i, sigma, stream=stream)
+        h, it, _ = code.decode(llr, max_iters=max_iters, alpha=alpha, early_stop=True,
+                               stream=stream)
+        st = code.frame_stats(info, h, it, max_iters, stream=stream)
+        if float(st[1].item()) / frames <= fer_max:
+            break
+    return float(b), float(max(b + 1.0, hi))
+
+
 def save_checkpoint(path: str, result: TrainResult) -> None:
     """Weights, Adam moments, step count, loss history and configuration as
     one torch file (tensors moved to the host)."""

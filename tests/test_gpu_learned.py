@@ -131,3 +131,59 @@ def test_paired_frame_errors(ldpc):
     want = [(~wa & ~wb).sum(), (~wa & wb).sum(), (wa & ~wb).sum(), (wa & wb).sum()]
     assert cnt.tolist() == [int(v) for v in want]
     assert want[2] > 0 and want[3] > 0
+
+
+# ------------------------------------------ past the weight table, give-up rule
+
+@pytest.mark.parametrize("shape,T,ebn0,frames,stops", [
+    (synth.wifi_n648_r12(), 8, 1.25, 401, ((4, 0.10), (10, 0.05))),
+    (synth.wifi_n1944_r56(), 6, 3.0, 203, ((3, 0.12), (9, 0.04))),
+    (synth.wimax_mixed_set()[-4], 8, 1.3, 37, ((5, 0.08), (0, 0.0))),
+    (synth.wimax_mixed_set()[3 * 4 + 2], 6, 2.0, 120, ((2, 0.3), (7, 0.02)))],
+    ids=["wifi648", "wifi1944", "wimax2304", "wimax36_r34"])
+def test_learned_past_table_with_checkpoints_bit_exact(ldpc, shape, T, ebn0, frames, stops):
+    """Iterations past the table repeat its last row; frames with too many
+    unsatisfied checks at a checkpoint stop there: hard decisions, counts
+    and posteriors equal the oracle's."""
+    rc, _, llr = _inputs(shape, frames, ebn0, frame0=31)
+    w = _weights(rc, T, 17, lo=0.5, hi=1.0)
+    si = (stops[0][0], stops[1][0])
+    sf = (stops[0][1], stops[1][1])
+    wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=20, stop_iter=si, stop_frac=sf)
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                     early_stop=True, want_post=True, max_iters=20,
+                                     stop_iter=si, stop_frac=sf)
+    assert (gi.cpu().numpy() == wi).all()
+    assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+    assert (gp.cpu().numpy() == wp).all()
+    assert wi.max() > T   # some frames ran past the table
+
+
+def test_learned_checkpoints_dynamic_handout(ldpc, request):
+    ldpc.set_grid_cap(1)
+    request.addfinalizer(lambda: ldpc.set_grid_cap(0))
+    shape = synth.wifi_n648_r12()
+    rc, _, llr = _inputs(shape, 160, 1.2, frame0=5)
+    w = _weights(rc, 5, 3, lo=0.6, hi=0.95)
+    wh, wi, _ = rc.decode_learned_f32(llr, w, max_iters=16, stop_iter=(3, 8),
+                                      stop_frac=(0.1, 0.04), want_post=False)
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, _ = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                    max_iters=16, stop_iter=(3, 8), stop_frac=(0.1, 0.04))
+    assert (gi.cpu().numpy() == wi).all() and (gh.cpu().numpy().view(np.uint32) == wh).all()
+    assert len(set(wi.tolist())) > 3
+
+
+def test_learned_ex_argument_checks(ldpc):
+    shape = synth.wifi_n648_r12()
+    code = ldpc.Code(shape.hbm, shape.z)
+    x = torch.zeros((4, code.n), dtype=torch.float32, device="cuda")
+    w = torch.full((3, code.nnz_blocks), 0.75, dtype=torch.float32, device="cuda")
+    with pytest.raises(ldpc.LdpcError):   # a checkpoint without early stop
+        code.decode_learned(x, w, early_stop=False, max_iters=5, stop_iter=(2, 0),
+                            stop_frac=(0.1, 0.0))
+    with pytest.raises(ldpc.LdpcError):   # negative limit
+        code.decode_learned(x, w, max_iters=5, stop_iter=(2, 0), stop_frac=(-0.1, 0.0))
+    with pytest.raises(ldpc.LdpcError):
+        code.decode_learned(x, w, max_iters=1001)

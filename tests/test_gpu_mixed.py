@@ -208,3 +208,34 @@ def test_mixed_learned_and_fallback(ldpc):
         wb[f] = (oracle.unpack_hard(fhw[a:b][None], c.n)[0][:c.k] != ref).any()
     assert cnt.tolist() == [int((~wa & ~wb).sum()), int((~wa & wb).sum()),
                             int((wa & ~wb).sum()), int((wa & wb).sum())]
+
+
+def test_mixed_learned_past_table_with_checkpoints(ldpc):
+    """The mixed learned launches with every code run up to 16 iterations
+    (rows past T_c repeating the last) and two give-up checkpoints equal the
+    oracle's decoder frame by frame."""
+    shapes = _shapes()
+    codes, cs, plan, batch = _setup(ldpc, shapes, 500, seed=21, ebn0=(1.0, 3.5))
+    rng = np.random.default_rng(8)
+    Ts = [int(rng.integers(3, 9)) for _ in shapes]
+    ws = [rng.uniform(0.55, 1.0, (T, c.nnz_blocks)).astype(np.float32) for T, c in zip(Ts, codes)]
+    plan.set_weights([torch.from_numpy(w).cuda() for w in ws])
+    si, sf = (4, 9), (0.1, 0.04)
+    hard, iters, post = plan.decode_learned(batch.llr, want_post=True, max_iters=16,
+                                            stop_iter=si, stop_frac=sf)
+    llr_h = batch.ref_llr
+    hw, it, pw = hard.cpu().numpy().view(np.uint32), iters.cpu().numpy(), post.cpu().numpy()
+    stopped = 0
+    for ci, s in enumerate(shapes):
+        idx = np.nonzero(plan.code_of_frame == ci)[0]
+        if idx.size == 0:
+            continue
+        rc = oracle.RefCode(s.hbm, s.z)
+        x = np.stack([llr_h[plan.llr_off[f]:plan.llr_off[f] + rc.n] for f in idx])
+        h, i, p = rc.decode_learned_f32(x, ws[ci], max_iters=16, stop_iter=si, stop_frac=sf)
+        stopped += int(((i == 4) | (i == 9)).sum())
+        for j, f in enumerate(idx):
+            a, b = plan.hard_off[f], plan.hard_off[f + 1]
+            assert it[f] == i[j] and (hw[a:b] == h[j]).all()
+            assert (pw[plan.llr_off[f]:plan.llr_off[f + 1]] == p[j]).all()
+    assert stopped > 0 and it.max() > max(Ts)
