@@ -811,14 +811,18 @@ static int stop_iter_of(const int *stop_iter, int j) { return stop_iter ? stop_i
 
 /* Learned normalised min-sum (see the header).  The weights of iteration k
  * are row min(k, T) - 1 of the table, so iterations past T repeat the last
- * row.  After each iteration with early_stop the unsatisfied checks u of the
- * hard decisions are counted: u = 0 stops the frame (eq. 21, Section 4
- * step 4); so does u > floor(stop_frac[j] * M) at iteration stop_iter[j]
- * (the give-up rule for frames the decoder is not converging on). */
-int ldpc_ref_decode_learned_f32(const ldpc_ref_code *c, const float *llr, int64_t frames,
-                                const float *weights, int T, int max_iters, int early_stop,
-                                const int *stop_iter, const float *stop_frac, uint32_t *hard,
-                                int32_t *iters, float *post) {
+ * row.  fused = 0 is the training arithmetic: the weighted message
+ * w * m is rounded, then added to or subtracted from the posterior; fused = 1
+ * is the inference arithmetic: Z - w m and Z + w m each with one rounding
+ * (fmaf), the unweighted messages m being kept per edge.  After each
+ * iteration with early_stop the unsatisfied checks u are counted: u = 0
+ * stops the frame (eq. 21, Section 4 step 4); so does u > floor(stop_frac[j]
+ * * M) at iteration stop_iter[j] (the give-up rule for frames the decoder is
+ * not converging on). */
+static int decode_learned(const ldpc_ref_code *c, const float *llr, int64_t frames,
+                          const float *weights, int T, int max_iters, int early_stop,
+                          const int *stop_iter, const float *stop_frac, int fused,
+                          uint32_t *hard, int32_t *iters, float *post) {
     ldpc_ref_params p = {max_iters, 1.0f, 0, early_stop};
     int st = check_params(c, &p, frames, llr, hard, iters);
     if (st) return st;
@@ -844,11 +848,15 @@ int ldpc_ref_decode_learned_f32(const ldpc_ref_code *c, const float *llr, int64_
     }
     for (int64_t f = 0; f < frames; f++) {
         for (int v = 0; v < n; v++) Zn[v] = llr[f * (int64_t)n + v];
+        /* L: the messages, weighted (fused = 0) or unweighted (fused = 1) */
         for (int e = 0; e < c->nnz; e++) L[e] = 0.0f;
         int done = max_iters;
         for (int k = 1; k <= max_iters; k++) {
-            const int row_w = (k < T ? k : T) - 1;
-            const float *wk = weights + (size_t)row_w * nnzb;
+            const float *wk = weights + (size_t)((k < T ? k : T) - 1) * nnzb;
+            /* the weights the old messages were made with (iteration k - 1;
+               iteration 1 has no old messages) */
+            const int kp = k > 1 ? k - 1 : 1;
+            const float *wp = weights + (size_t)((kp < T ? kp : T) - 1) * nnzb;
             for (int i = 0; i < c->mb; i++) {
                 const int q0 = block_edge_base(c, i);
                 for (int r = 0; r < c->z; r++) {
@@ -856,12 +864,16 @@ int ldpc_ref_decode_learned_f32(const ldpc_ref_code *c, const float *llr, int64_
                     int b = c->row_start[row];
                     int d = c->row_start[row + 1] - b;
                     for (int t = 0; t < d; t++)                       /* eq. (22) */
-                        Q[t] = Zn[c->row_var[b + t]] - L[b + t];
-                    for (int t = 0; t < d; t++)                       /* eq. (23), weighted */
-                        Ln[t] = wk[q0 + t] * minsum_excl_f32(Q, d, t);
+                        Q[t] = fused ? fmaf(-wp[q0 + t], L[b + t], Zn[c->row_var[b + t]])
+                                     : Zn[c->row_var[b + t]] - L[b + t];
+                    for (int t = 0; t < d; t++) {                     /* eq. (23) */
+                        const float m = minsum_excl_f32(Q, d, t);
+                        Ln[t] = fused ? m : wk[q0 + t] * m;
+                    }
                     for (int t = 0; t < d; t++) {                     /* eq. (20) */
                         L[b + t] = Ln[t];
-                        Zn[c->row_var[b + t]] = Q[t] + Ln[t];
+                        Zn[c->row_var[b + t]] = fused ? fmaf(wk[q0 + t], Ln[t], Q[t])
+                                                      : Q[t] + Ln[t];
                     }
                 }
             }
@@ -883,10 +895,18 @@ int ldpc_ref_decode_learned_f32(const ldpc_ref_code *c, const float *llr, int64_
     return LDPC_REF_OK;
 }
 
+int ldpc_ref_decode_learned_f32(const ldpc_ref_code *c, const float *llr, int64_t frames,
+                                const float *weights, int T, int max_iters, int early_stop,
+                                const int *stop_iter, const float *stop_frac, uint32_t *hard,
+                                int32_t *iters, float *post) {
+    return decode_learned(c, llr, frames, weights, T, max_iters, early_stop, stop_iter,
+                          stop_frac, 1, hard, iters, post);
+}
+
 int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *c, const float *llr,
                                          int64_t frames, const float *weights, int T,
                                          int early_stop, uint32_t *hard, int32_t *iters,
                                          float *post) {
-    return ldpc_ref_decode_learned_f32(c, llr, frames, weights, T, T, early_stop, NULL, NULL,
-                                       hard, iters, post);
+    return decode_learned(c, llr, frames, weights, T, T, early_stop, NULL, NULL, 0, hard,
+                          iters, post);
 }

@@ -28,11 +28,13 @@
  *     bounds, FP32 = int8 where nothing saturates, the counted saturations
  *     (tests/test_oracle_decoder.py);
  *   weighted (learned) decoder: the worked example with weights, constant
- *     weights = the alpha decoder (tests/test_oracle_decoder.py); run past
- *     its table and with give-up checkpoints: equal to an explicitly
- *     extended table, to a shorter decode where the checkpoint always fires,
- *     to the plain run where it never does, and checkpoint decisions against
- *     syndrome weights from a dense H (tests/test_oracle_learned_gated.py);
+ *     weights = the alpha decoder (tests/test_oracle_decoder.py); the
+ *     inference form (fused updates, run past its table, give-up
+ *     checkpoints): an exact-rational trace on tiny codes, power-of-two
+ *     weights = the alpha decoder, equal to an explicitly extended table, to
+ *     a shorter decode where a checkpoint always fires, to the plain run
+ *     where it never does, and checkpoint decisions against syndrome
+ *     weights from a dense H (tests/test_oracle_learned_gated.py);
  *   flooding: equal to layered on one layer (tests/test_oracle_decoder.py);
  *   int16 wrap decoder, bitmap encoder: hand-worked overflow traces, FP32 /
  *     int8 equivalence without overflow, brute-force rotation, the byte
@@ -138,15 +140,18 @@ int ldpc_ref_decode_layered_weighted_f32(const ldpc_ref_code *code, const float 
                                          int64_t frames, const float *weights, int T,
                                          int early_stop, uint32_t *hard, int32_t *iters,
                                          float *post);
-/* The learned decoder run past its weight table, with a give-up rule (an
- * extension, not in the paper): iteration k uses weight row min(k, T) - 1,
- * so iterations T+1..max_iters repeat the last row.  With early_stop the
- * unsatisfied checks u of the hard decisions are counted after every
- * iteration; the frame stops at iteration k when u = 0, or when k equals
- * stop_iter[j] (j = 0, 1; 0 means no checkpoint) and u > floor(stop_frac[j]
- * * M) with the product rounded in FP32.  stop_iter / stop_frac may be NULL
- * (no checkpoints); checkpoints need early_stop.  The weighted decoder above
- * is the case max_iters = T without checkpoints. */
+/* The learned decoder as the library runs it for inference (extensions, not
+ * in the paper): the message of edge e in iteration k is w[row][q] * m with
+ * m the eq. (23) min-sum message and row = min(k, T) - 1, so iterations
+ * past T repeat the last row; the posterior updates Z_mn = Z_n - w' m_old
+ * (w' the weight m_old was made with) and Z_n = Z_mn + w m are each rounded
+ * once (fused multiply-add, C99 fmaf).  The weighted decoder above rounds
+ * w * m first (the training arithmetic).  With early_stop the unsatisfied
+ * checks u of the hard decisions are counted after every iteration; the
+ * frame stops at iteration k when u = 0, or when k equals stop_iter[j]
+ * (j = 0, 1; 0 means no checkpoint) and u > floor(stop_frac[j] * M) with
+ * the product rounded in FP32.  stop_iter / stop_frac may be NULL (no
+ * checkpoints); checkpoints need early_stop. */
 int ldpc_ref_decode_learned_f32(const ldpc_ref_code *code, const float *llr, int64_t frames,
                                 const float *weights, int T, int max_iters, int early_stop,
                                 const int *stop_iter, const float *stop_frac, uint32_t *hard,
