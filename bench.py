@@ -37,9 +37,10 @@ WORKLOAD = ("wifi6-shaped N=1944 Z=81 R=5/6 (seeded 4x24 base matrix, seed 2), "
             "3 x 262144 frames at Eb/N0 3.5/4.0/4.5 dB, max 20 iterations, early stop")
 METRIC = "info Gbit/s at matched FER, learned-NMS vs plain min-sum; % roofline"
 METRIC_BASIS = ("value: info Gbit/s of the plain int8 layered min-sum decoder on the batched "
-                "N=1944 workload (the workload this metric is quoted on); % roofline: "
-                "roofline.frac; learned-NMS against plain min-sum at matched FER: the "
-                "learned (N=648) and learned_scale (mixed set) objects")
+                "N=1944 workload (fp32: the same frames in FP32, the like-for-like figure "
+                "against the paper's float decoder); % roofline: roofline.frac; learned-NMS "
+                "against plain min-sum at matched FER: learned_vs_plain (summary of the "
+                "learned_scale and learned objects)")
 # Algorithmic operations per edge per iteration (per frame, or per packed
 # word of four frames), the scope table's count: pass 1 = 9 (old message
 # rebuilt by a select and a sign, subtract, |.|, two compare/select pairs for
@@ -225,8 +226,12 @@ def learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
         return (torch.empty((F, code.nwords), dtype=torch.int32, device=dev),
                 torch.empty((F,), dtype=torch.int32, device=dev), None)
 
-    outs = {k: out() for k in ("plain_i8_20", "plain_f32_20", "learned", "learned_fallback")}
+    names = ("plain_i8_20", "plain_f32_20", "learned", "learned_fallback", "learned_gated",
+             "learned_20", "ablation_const_gated")
+    outs = {k: out() for k in names}
     fb_frames = [0]
+    w_const = torch.full_like(w, 0.75)
+    gate = dict(max_iters=MAX_ITERS, stop_iter=GATE_ITERS, stop_frac=GATE_FRACS)
 
     def run(name):
         o = outs[name]
@@ -237,6 +242,12 @@ def learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
                         out=o)
         elif name == "learned":
             code.decode_learned(llr, w, early_stop=True, out=o)
+        elif name == "learned_gated":
+            code.decode_learned(llr, w, out=o, **gate)
+        elif name == "learned_20":
+            code.decode_learned(llr, w, out=o, max_iters=MAX_ITERS)
+        elif name == "ablation_const_gated":
+            code.decode_learned(llr, w_const, out=o, **gate)
         else:
             _, _, fb_frames[0] = code.decode_learned_fallback(llr, w, MAX_ITERS, workspace=wsfb,
                                                               out=(o[0], o[1]))
@@ -270,14 +281,21 @@ def learned_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
         reduce_counters(np.array([fb_frames[0]], dtype=np.int64))[0])
     comps = {}
     for plain in ("plain_i8_20", "plain_f32_20"):
-        for lrn in ("learned", "learned_fallback"):
+        for lrn in names[2:]:
             cnt = reduce_counters(code.paired_frame_errors(info, outs[lrn][0],
                                                            outs[plain][0]).cpu().numpy())
             c = stats.compare(cnt, F * ws)
             c["speedup"] = res[lrn]["value"] / res[plain]["value"]
             comps[f"{lrn}_vs_{plain}"] = c
+    wstat = {str(t + 1): {"mean": float(w[t].mean()), "min": float(w[t].min()),
+                          "max": float(w[t].max())} for t in range(w.shape[0])}
     return {"workload": LEARNED_WORKLOAD, "frames": F * ws, "T": T,
-            "decoders": res, "comparisons": comps,
+            "decoders": res, "comparisons": comps, "weights_per_iteration": wstat,
+            "decoder_notes": {"learned_gated": f"up to {MAX_ITERS} iterations (rows past T "
+                                               "repeat the last), give-up checkpoints "
+                                               f"{list(zip(GATE_ITERS, GATE_FRACS))}",
+                              "learned_20": f"up to {MAX_ITERS} iterations, no checkpoints",
+                              "ablation_const_gated": "learned_gated with every weight 0.75"},
             "matched_fer_test": "exact one-sided McNemar on paired frame outcomes; matched = "
                                 "learned not worse at the 5 % level",
             "training": {"steps": cfg.steps, "batch": cfg.batch, "lr": cfg.lr,
@@ -402,21 +420,84 @@ SCALE_WORKLOAD = ("learned vs plain at scale: the 76 WiMAX-shaped codes plus the
                   "(seed 3), Eb/N0 uniform in [1.5, 4.5) dB per frame")
 
 
+def _frame_errors_mixed(ldpc, torch, plan, codes, info, hard):
+    """Per-frame info-bit error flags of a mixed batch (bool[frames] on the
+    GPU), from the plan layout: analysis of the decoded frames, untimed."""
+    dev = hard.device
+    err = torch.zeros(plan.frames, dtype=torch.bool, device=dev)
+    cof = plan.code_of_frame
+    shifts = torch.arange(32, device=dev, dtype=torch.int32)
+    for ci, code in enumerate(codes):
+        idx = np.nonzero(cof == ci)[0]
+        if idx.size == 0:
+            continue
+        nw = (code.k + 31) // 32
+        hw = torch.from_numpy(plan.hard_off[idx]).to(dev)[:, None] + torch.arange(nw, device=dev)
+        bits = ((hard[hw].unsqueeze(-1) >> shifts) & 1).reshape(idx.size, -1)[:, :code.k]
+        io = torch.from_numpy(plan.info_off[idx]).to(dev)[:, None] + torch.arange(code.k,
+                                                                                  device=dev)
+        err[torch.from_numpy(idx).to(dev)] = (bits.to(torch.uint8) != info[io]).any(dim=1)
+    return err
+
+
+def _mixed_ebn0(ldpc, torch, plan, codes, first, lo_hi):
+    """Per-frame Eb/N0 (dB) of a mixed batch, regenerated with the batch's own
+    draws (ldpc_snr_sigma is deterministic in the frame identity)."""
+    from paper_2306_12063_gb300.workload import mixed_frame_id
+    eb = np.zeros(plan.frames, dtype=np.float64)
+    cof = plan.code_of_frame
+    for ci, code in enumerate(codes):
+        idx = np.nonzero(cof == ci)[0]
+        if idx.size == 0:
+            continue
+        rate = code.k / code.n
+        sig = ldpc.snr_sigma(1, mixed_frame_id(ci, first), int(idx.size), lo_hi[0], lo_hi[1], rate,
+                             device=codes[0].device).double().cpu().numpy()
+        eb[idx] = 10.0 * np.log10(1.0 / (2.0 * rate * sig * sig))
+    return eb
+
+
+EBN0_BINS = (1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5)
+
+
+def _per_bin(err_np, eb, iters_np):
+    out = []
+    for lo, hi in zip(EBN0_BINS, EBN0_BINS[1:]):
+        m = (eb >= lo) & (eb < hi)
+        n = int(m.sum())
+        out.append({"ebn0_db": [lo, hi], "frames": n,
+                    "fer": float(err_np[m].mean()) if n else None,
+                    "mean_iters": float(iters_np[m].mean()) if n else None})
+    return out
+
+
+# Give-up checkpoints of the learned pipeline: at iteration 4 a frame with
+# more than 10 % of its checks unsatisfied stops, at iteration 10 one with
+# more than 5 %; frames are otherwise decoded up to 20 iterations.
+GATE_ITERS = (4, 10)
+GATE_FRACS = (0.10, 0.05)
+
+
 def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
-    """Learned normalised min-sum (per-code weights, T = 8 up to rate 2/3 and
-    6 above) with its int8 plain fallback against plain min-sum at 20
-    iterations on the same mixed batch, plus the oracle's FER of the learned
-    pipeline on a subset of the frames."""
+    """Learned normalised min-sum at scale (per-code weights) against plain
+    min-sum at 20 iterations on the same mixed batch.  Decoders, all timed:
+    plain int8 / FP32 at 20 iterations; the learned decoder at T_c
+    iterations and with its int8 fallback (the recipe's pipeline); and the
+    learned pipeline run up to 20 iterations with the give-up checkpoints,
+    with weights trained over each code's operating range.  Ablation on the
+    same frames: the same pipeline with constant 0.75 weights (plain FP32
+    min-sum plus the checkpoints) and with weights trained on the recipe's
+    common [1, 4] dB.  FER per Eb/N0 bin, McNemar against plain, the
+    weights' statistics per iteration, and the oracle's decode of a subset."""
     from paper_2306_12063_gb300 import stats, train
     from paper_2306_12063_gb300.mixed_learned import decode_learned_fallback
-    from paper_2306_12063_gb300.shard import reduce_counters
+    from paper_2306_12063_gb300.shard import mixed_shard, reduce_counters
     from paper_2306_12063_gb300.workload import make_mixed_batch
 
     shapes = synth.wimax_mixed_set() + [synth.wifi_n648_r12(), synth.wifi_n1944_r56()]
     codes = [ldpc.Code(s.hbm, s.z, device=dev) for s in shapes]
     cs = ldpc.CodeSet(codes)
     F = args.scale_frames
-    from paper_2306_12063_gb300.shard import mixed_shard
     first, cof = mixed_shard(synth.mixed_frame_assignment(len(shapes), F * ws, seed=3)[0], rank,
                              ws)
     plan = ldpc.MixedPlan(cs, cof)
@@ -424,24 +505,33 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     counts = np.bincount(cof, minlength=len(shapes))
     # per-code training on the library's own generators (bounded budget)
     t0 = time.time()
-    weights = []
+    w_range, w_recipe, ranges = [], [], []
     for ci, code in enumerate(codes):
         if counts[ci] == 0:
-            weights.append(None)
+            w_range.append(None)
+            w_recipe.append(None)
+            ranges.append(None)
             continue
         T = train.default_iterations(code.k / code.n)
-        cfg = train.TrainConfig(T=T, steps=args.scale_train_steps, batch=1024, lr=2e-3,
-                                seed=1000 + ci)
-        weights.append(train.train_weights(code, cfg).weights)
+        rng_c = train.operating_range(code, LEARNED_EBN0[0], LEARNED_EBN0[1])
+        ranges.append(rng_c)
+        base = dict(T=T, steps=args.scale_train_steps, batch=1024, lr=2e-3, seed=1000 + ci)
+        w_range.append(train.train_weights(code, train.TrainConfig(ebn0_db=rng_c, **base)).weights)
+        w_recipe.append(train.train_weights(code, train.TrainConfig(**base)).weights)
+    w_const = [None if w is None else torch.full_like(w, 0.75) for w in w_range]
     torch.cuda.synchronize()
     train_s = time.time() - t0
-    plan.set_weights(weights)
     q = plan.quantize(batch.llr)
-    outs = {k: plan.empty_outputs() for k in ("plain_i8_20", "plain_f32_20", "learned",
-                                               "learned_fallback")}
+    names = ("plain_i8_20", "plain_f32_20", "learned", "learned_fallback", "learned_gated",
+             "ablation_const_gated", "ablation_recipe_gated", "ablation_range_20")
+    outs = {k: plan.empty_outputs() for k in names}
     plan.autotune(q, ldpc.I8X4, max_iters=MAX_ITERS, reps=2, out=outs["plain_i8_20"])
     plan.autotune(batch.llr, ldpc.F32, max_iters=MAX_ITERS, reps=2, out=outs["plain_f32_20"])
     fbn = [0]
+    gate = dict(max_iters=MAX_ITERS, stop_iter=GATE_ITERS, stop_frac=GATE_FRACS)
+    weights_of = {"learned": w_range, "learned_fallback": w_range, "learned_gated": w_range,
+                  "ablation_const_gated": w_const, "ablation_recipe_gated": w_recipe,
+                  "ablation_range_20": w_range}
 
     def run(name):
         o = outs[name]
@@ -451,13 +541,23 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
             plan.decode(batch.llr, ldpc.F32, max_iters=MAX_ITERS, out=(o[0], o[1], None))
         elif name == "learned":
             plan.decode_learned(batch.llr, early_stop=True, out=(o[0], o[1], None))
-        else:
+        elif name == "learned_fallback":
             _, _, fbn[0] = decode_learned_fallback(plan, batch.llr, MAX_ITERS, out=o)
+        elif name == "ablation_range_20":
+            plan.decode_learned(batch.llr, out=(o[0], o[1], None), max_iters=MAX_ITERS)
+        else:
+            plan.decode_learned(batch.llr, out=(o[0], o[1], None), **gate)
+
 
     steps = max(1, args.steps // 4)
     res = {}
     info_bits = plan.info_elems * ws
-    for name in outs:
+    nf = F * ws
+    eb = _mixed_ebn0(ldpc, torch, plan, codes, first, LEARNED_EBN0)
+    errs = {}
+    for name in names:
+        if name in weights_of:
+            plan.set_weights(weights_of[name])   # outside the timed region
         for _ in range(2):
             run(name)
         barrier()
@@ -477,40 +577,72 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
         mi = 28 if name == "learned_fallback" else MAX_ITERS
         cnt, _ = plan.stats(batch.info, outs[name][0], outs[name][1], mi, per_code=False)
         st = reduce_counters(cnt.cpu().numpy())
-        nf = F * ws
+        e = _frame_errors_mixed(ldpc, torch, plan, codes, batch.info, outs[name][0])
+        errs[name] = e
         res[name] = {"value": info_bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms": ms,
                      "fer": float(st[1]) / nf, "wilson95": stats.wilson_interval(int(st[1]), nf),
-                     "mean_iters": float(st[3]) / nf}
+                     "mean_iters": float(st[3]) / nf,
+                     "per_ebn0_bin": _per_bin(e.cpu().numpy(), eb,
+                                              outs[name][1].cpu().numpy())}
+    plan.set_weights(w_range)
     res["learned_fallback"]["fallback_frames"] = int(
         reduce_counters(np.array([fbn[0]], dtype=np.int64))[0])
     comps = {}
     for plain in ("plain_i8_20", "plain_f32_20"):
-        for lrn in ("learned", "learned_fallback"):
+        for lrn in names[2:]:
             cnt = reduce_counters(plan.paired_errors(batch.info, outs[lrn][0],
                                                      outs[plain][0]).cpu().numpy())
-            c = stats.compare(cnt, F * ws)
+            c = stats.compare(cnt, nf)
             c["speedup"] = res[lrn]["value"] / res[plain]["value"]
             comps[f"{lrn}_vs_{plain}"] = c
-    out = {"workload": SCALE_WORKLOAD, "frames": F * ws, "codes": len(shapes),
+    wstat = {}
+    Tmax = max(w.shape[0] for w in w_range if w is not None)
+    for t in range(Tmax):
+        rows = torch.cat([w[t] for w in w_range if w is not None and w.shape[0] > t])
+        wstat[str(t + 1)] = {"mean": float(rows.mean()), "min": float(rows.min()),
+                             "max": float(rows.max())}
+    lo_c = [r[0] for r in ranges if r is not None]
+    out = {"workload": SCALE_WORKLOAD, "frames": nf, "codes": len(shapes),
            "decoders": res, "comparisons": comps,
+           "decoder_notes": {
+               "learned": "operating-range weights, T_c iterations (8 up to rate 2/3, else 6)",
+               "learned_fallback": "learned, then int8 plain min-sum (20 iterations) on "
+                                   "the frames with a nonzero syndrome",
+               "learned_gated": f"operating-range weights, up to {MAX_ITERS} iterations "
+                                "(rows past T_c repeat the last), give-up checkpoints "
+                                f"{list(zip(GATE_ITERS, GATE_FRACS))} (iteration, "
+                                "unsatisfied-check fraction of M)",
+               "ablation_const_gated": "the learned_gated pipeline with every weight 0.75 "
+                                       "(plain FP32 min-sum plus the checkpoints)",
+               "ablation_recipe_gated": "the learned_gated pipeline with weights trained on "
+                                        "the recipe's common [1, 4] dB",
+               "ablation_range_20": "operating-range weights, up to 20 iterations, no "
+                                    "checkpoints"},
+           "weights_per_iteration": wstat,
            "training": {"per_code": {"steps": args.scale_train_steps, "batch": 1024, "lr": 2e-3,
-                                     "ebn0_db": [1.0, 4.0], "T": "8 (R <= 2/3), 6 (R > 2/3)"},
+                                     "T": "8 (R <= 2/3), 6 (R > 2/3)",
+                                     "operating_range": "[b, max(b + 1, 4.5)] dB, b the lowest "
+                                     "0.25 dB step from 1.5 where plain FP32-20 FER <= 0.5 on "
+                                     "4,096 calibration frames",
+                                     "recipe_range_db": [1.0, 4.0]},
+                        "range_lower_db": {"min": min(lo_c), "max": max(lo_c),
+                                           "mean": float(np.mean(lo_c))},
                         "codes_trained": int((counts > 0).sum()), "seconds": train_s}}
-    # the oracle's FER of the learned pipeline on a subset (rank 0)
     if rank == 0 and args.scale_oracle_frames > 0:
-        out["oracle_subset"] = _oracle_learned_subset(plan, shapes, weights, batch,
-                                                      outs["learned_fallback"],
+        out["oracle_subset"] = _oracle_learned_subset(plan, shapes, w_range, batch,
+                                                      outs["learned_gated"],
                                                       args.scale_oracle_frames, first)
     return out
 
 
-def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub, frame_base):
-    """The oracle's learned-then-int8-fallback decode of the first nsub frames
-    (thread pool over codes), on frames the oracle generates itself from the
-    batch's definition (frame j of code c at identity c * 2^32 + frame_base
-    + j); the learned weights, the decoder's parameters, are the ones the GPU
-    trained.  Reports how many of those frames' LLRs equal the GPU batch's,
-    the oracle's FER and how many hard decisions equal the GPU pipeline's."""
+def _oracle_learned_subset(plan, shapes, weights, batch, gated_out, nsub, frame_base):
+    """The oracle's gated learned decode (up to 20 iterations, the give-up
+    checkpoints) of the first nsub frames (thread pool over codes), on frames
+    the oracle generates itself from the batch's definition (frame j of code
+    c at identity c * 2^32 + frame_base + j); the learned weights, the
+    decoder's parameters, are the ones the GPU trained.  Reports how many of
+    those frames' LLRs equal the GPU batch's, the oracle's FER and how many
+    hard decisions and iteration counts equal the GPU's."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     nsub = min(nsub, plan.frames)
@@ -522,7 +654,8 @@ def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub, frame_bas
     gpu_llr = batch.llr[:int(plan.llr_off[nsub])].cpu().numpy()
     inputs_equal = sum(int((gpu_llr[plan.llr_off[f]:plan.llr_off[f + 1]].view(np.uint32) ==
                             llr_l[f].view(np.uint32)).all()) for f in range(nsub))
-    gpu_h = fb_out[0][:int(plan.hard_off[nsub])].cpu().numpy().view(np.uint32)
+    gpu_h = gated_out[0][:int(plan.hard_off[nsub])].cpu().numpy().view(np.uint32)
+    gpu_i = gated_out[1][:nsub].cpu().numpy()
 
     def one(ci):
         idx = np.nonzero(cof == ci)[0]
@@ -532,22 +665,16 @@ def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub, frame_bas
         rc = oracle.RefCode(s.hbm, s.z)
         w = weights[ci].cpu().numpy()
         x = np.stack([llr[plan.llr_off[f]:plan.llr_off[f] + rc.n] for f in idx])
-        h, _, _ = rc.decode_layered_weighted_f32(x, w, w.shape[0], early_stop=True,
-                                                 want_post=False)
-        bits = oracle.unpack_hard(h, rc.n)
-        bad = np.array([rc.syndrome_weight(b) != 0 for b in bits])
-        if bad.any():
-            h8, _, _, _ = rc.decode_layered_i8(oracle.quantize_i8(x[bad]), MAX_ITERS, True,
-                                               True, want_post=False)
-            h = h.copy()
-            h[bad] = h8
+        h, it, _ = rc.decode_learned_f32(x, w, max_iters=MAX_ITERS, stop_iter=GATE_ITERS,
+                                         stop_frac=GATE_FRACS, want_post=False)
         bits = oracle.unpack_hard(h, rc.n)
         fe = 0
         same = 0
         for j, f in enumerate(idx):
             ref = info[plan.info_off[f]:plan.info_off[f + 1]]
             fe += int((bits[j][:rc.k] != ref).any())
-            same += int((gpu_h[plan.hard_off[f]:plan.hard_off[f + 1]] == h[j]).all())
+            same += int((gpu_h[plan.hard_off[f]:plan.hard_off[f + 1]] == h[j]).all() and
+                        gpu_i[f] == it[j])
         return idx.size, fe, same
 
     t0 = time.time()
@@ -556,8 +683,9 @@ def _oracle_learned_subset(plan, shapes, weights, batch, fb_out, nsub, frame_bas
     n = sum(p[0] for p in parts)
     fe = sum(p[1] for p in parts)
     same = sum(p[2] for p in parts)
-    return {"frames": n, "fer": fe / max(n, 1), "frames_equal_to_gpu": same,
-            "inputs_equal_to_gpu": inputs_equal, "seconds": time.time() - t0}
+    return {"decoder": "learned_gated", "frames": n, "fer": fe / max(n, 1),
+            "frames_equal_to_gpu": same, "inputs_equal_to_gpu": inputs_equal,
+            "seconds": time.time() - t0}
 
 
 # Tab. 5 of the paper (data-bit throughput, WiMAX N=2304 R=5/6, fixed 10
@@ -1094,6 +1222,26 @@ def main():
                 "gpu_launches": len(EBN0) * args.steps, "clocks": i8_clk,
                 "mean_iters": i8_iters / (len(EBN0) * F), "fer": fer}
         line.update(res)
+        lvp = {}
+        for key, leg in (("mixed_78_codes", "learned_scale"), ("n648", "learned")):
+            if leg not in res:
+                continue
+            L = res[leg]
+            dec = L["decoders"]
+            c32 = L["comparisons"]["learned_gated_vs_plain_f32_20"]
+            c8 = L["comparisons"]["learned_gated_vs_plain_i8_20"]
+            lvp[key] = {"workload": L["workload"], "learned_decoder": "learned_gated",
+                        "value": dec["learned_gated"]["value"],
+                        "plain_f32_20": dec["plain_f32_20"]["value"],
+                        "ratio_vs_plain_f32_20": c32["speedup"], "matched_f32": c32["matched"],
+                        "mcnemar_p_learned_worse_f32": c32["mcnemar_p_a_worse"],
+                        "fer": dec["learned_gated"]["fer"],
+                        "fer_plain_f32_20": dec["plain_f32_20"]["fer"],
+                        "plain_i8_20": dec["plain_i8_20"]["value"],
+                        "ratio_vs_plain_i8_20": c8["speedup"], "matched_i8": c8["matched"],
+                        "fer_plain_i8_20": dec["plain_i8_20"]["fer"]}
+        if lvp:
+            line["learned_vs_plain"] = lvp
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

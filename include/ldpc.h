@@ -179,9 +179,11 @@ ldpc_status ldpc_decode_layered_minsum(const ldpc_code *code, ldpc_dtype dtype,
  * nonzero block of H_bm: L_mn = w[k-1][q] * min_{n' != n} |Z_mn'| *
  * prod sgn Z_mn', where q numbers the nonzero blocks of H_bm row by row in
  * increasing block column (q = 0 .. nnz(H_bm)-1).  The paper's decoder is
- * the special case of all weights 1 (eq. 23).  d_weights: device
- * float[T][nnz(H_bm)]; at most T iterations, with the syndrome stop when
- * early_stop = 1.  Other arguments and layouts as in
+ * the special case of all weights 1 (eq. 23).  The weighted message is
+ * applied with one rounding per update: Z_mn = Z_n - w' m_old and
+ * Z_n = Z_mn + w m are fused multiply-adds (w' the weight m_old was made
+ * with).  d_weights: device float[T][nnz(H_bm)]; at most T iterations, with
+ * the syndrome stop when early_stop = 1.  Other arguments and layouts as in
  * ldpc_decode_layered_minsum with dtype LDPC_F32. */
 ldpc_status ldpc_decode_learned_minsum(const ldpc_code *code, const float *d_llr,
                                        int64_t frames, const float *d_weights, int T,
@@ -251,8 +253,10 @@ ldpc_status ldpc_decode_learned_fallback(const ldpc_code *code, const float *d_l
  * decodes with fixed messages; this is the unrolled layered decoder of
  * Section 4 differentiated in reverse mode). ---- */
 
-/* Training forward: exactly T iterations of ldpc_decode_learned_minsum (no
- * syndrome stop) on every frame, and its loss
+/* Training forward: exactly T iterations of the learned decoder (no
+ * syndrome stop) on every frame, with the weighted message w m rounded
+ * before it is added or subtracted (the form the gradients below are exact
+ * for; inference fuses the two), and its loss
  *   loss[f] = sum over t = 1..T and n of BCE(sigmoid(-Z_n^(t)), c_n)
  *           = softplus(-Z) + c Z,
  * the cross-entropy of each iteration's posterior bit probability against
@@ -264,8 +268,7 @@ ldpc_status ldpc_decode_learned_fallback(const ldpc_code *code, const float *d_l
  * (unscaled smallest and second smallest |Z_mn| as float bits, argmin
  * edge, message sign bits; may be NULL when T = 1); d_loss float[frames];
  * d_loss_sum (float[1] or NULL) = loss_scale * sum_f d_loss[f], summed in a
- * fixed order.  The posteriors equal those of the inference decoder bit for
- * bit. */
+ * fixed order. */
 ldpc_status ldpc_learned_train_forward(const ldpc_code *code, const float *d_llr,
                                        const uint8_t *d_bits, int64_t frames,
                                        const float *d_weights, int T, float *d_post,

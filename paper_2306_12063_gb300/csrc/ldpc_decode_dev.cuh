@@ -123,14 +123,15 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 // posterior is +inf: |Z_mn| = +inf is never a minimum and its sign is +.
 //
 // WT (learned normalised min-sum): the message of edge q in iteration k is
-// w[k-1][q] times the unscaled magnitude, q numbering the nonzero blocks of
-// H_bm row by row.  The row state then keeps the unscaled minima and the
-// message signs before weighting.  wprev / wcur point at this layer's
-// weights of the previous and the current iteration, staged in shared memory
-// in slot order (wpad(DMAX) floats per layer, 16-byte aligned, zero in the
-// leading unused slots).  Since rounding is symmetric in sign,
-// (w |m|) with the sign of m applied afterwards equals w m: one multiply per
-// slot on the signed message.
+// w[k-1][q] times the unscaled min-sum message m, q numbering the nonzero
+// blocks of H_bm row by row.  The row state then keeps the unscaled minima
+// and the message signs before weighting.  wprev / wcur point at this
+// layer's weights of the previous and the current iteration, staged in
+// shared memory in slot order (wpad(DMAX) floats per layer, 16-byte
+// aligned, zero in the leading unused slots).  The posterior updates
+// Z_mn = Z_n - w' m_old and Z_n = Z_mn + w m are each one fused
+// multiply-add (one rounding), so the learned row costs what the plain one
+// does.
 __host__ __device__ constexpr int wpad(int dmax) { return (dmax + 3) & ~3; }
 
 template <int DS, int DMAX, bool WT = false>
@@ -176,8 +177,8 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
             // on the FMA pipe)
             const uint32_t sbit = (meta * (1u << (i + 32 - DMAX))) & 0x80000000u;
             const float Lu = __uint_as_float(__float_as_uint(mag) | sbit);
-            const float L = WT ? __fmul_rn(wp[WT ? i : 0], Lu) : Lu;
-            const float q = __fsub_rn(Q[i], L);
+            // learned weights: Z - w' m_old rounded once (fused)
+            const float q = WT ? __fmaf_rn(-wp[WT ? i : 0], Lu, Q[i]) : __fsub_rn(Q[i], Lu);
             Q[i] = q;
             const float a = fabsf(q);
             mn2 = fmaxf(mn1, fminf(mn2, a));
@@ -198,12 +199,12 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
             const uint32_t ms = at_min ? s2 : s1;
             id = at_min ? i : id;
             const uint32_t L = ms ^ (__float_as_uint(Q[i]) & 0x80000000u);
-            // learned weights: w times the signed message
-            const uint32_t Lw = WT ? __float_as_uint(__fmul_rn(wc[WT ? i : 0], __uint_as_float(L)))
-                                   : L;
             // unconditional: a leading unused slot stores +inf + L = +inf back
-            // into the dummy posterior
-            sts_u32(Zs, off[i], __float_as_uint(__fadd_rn(Q[i], __uint_as_float(Lw))));
+            // into the dummy posterior (learned: weight 0 there); learned
+            // weights: Z_mn + w m rounded once (fused)
+            const float zn = WT ? __fmaf_rn(wc[WT ? i : 0], __uint_as_float(L), Q[i])
+                                : __fadd_rn(Q[i], __uint_as_float(L));
+            sts_u32(Zs, off[i], __float_as_uint(zn));
             nsg = __funnelshift_l(L, nsg, 1);
         }
         rs[0] = __float_as_uint(n1);

@@ -54,7 +54,7 @@ for shape in (synth.wifi_n648_r12(), synth.wifi_n1944_r56(), synth.tiny_z3_code(
     code.sync()
     assert (gi.cpu().numpy() == wi).all() and (gp.cpu().numpy() == wp).all()
     w = np.random.default_rng(2).uniform(0.5, 1.0, (4, rc.nnz_blocks)).astype(np.float32)
-    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, 4, early_stop=True)
+    wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=4, early_stop=True)
     gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
                                      early_stop=True, want_post=True)
     code.sync()

@@ -41,7 +41,7 @@ def _weights(rc, T, seed, lo=0.4, hi=1.0):
 def test_learned_bit_exact(ldpc, shape, T, ebn0, frames):
     rc, _, llr = _inputs(shape, frames, ebn0)
     w = _weights(rc, T, 5)
-    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, T, early_stop=True)
+    wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=T, early_stop=True)
     code = ldpc.Code(shape.hbm, shape.z)
     gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
                                      early_stop=True, want_post=True)
@@ -55,21 +55,25 @@ def test_learned_negative_and_mixed_weights(ldpc):
     shape = synth.wifi_n648_r12()
     rc, _, llr = _inputs(shape, 64, 2.5)
     w = _weights(rc, 5, 9, lo=-0.3, hi=1.2)
-    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, 5, early_stop=False)
+    wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=5, early_stop=False)
     code = ldpc.Code(shape.hbm, shape.z)
     gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
                                      early_stop=False, want_post=True)
     assert (gp.cpu().numpy() == wp).all() and (gi.cpu().numpy() == wi).all()
 
 
-def test_learned_constant_weights_equal_normalised(ldpc):
+@pytest.mark.parametrize("wval,alpha,normalise", [(0.5, 0.5, True), (1.0, 1.0, False)])
+def test_learned_power_of_two_weights_equal_normalised(ldpc, wval, alpha, normalise):
+    """Power-of-two weights make every product exact, so the fused learned
+    updates equal the alpha decoder's."""
     shape = synth.wifi_n1944_r56()
     rc, _, llr = _inputs(shape, 200, 4.0)
     code = ldpc.Code(shape.hbm, shape.z)
-    w = torch.full((8, rc.nnz_blocks), 0.75, dtype=torch.float32, device="cuda")
+    w = torch.full((8, rc.nnz_blocks), wval, dtype=torch.float32, device="cuda")
     x = torch.from_numpy(llr).cuda()
     a = code.decode_learned(x, w, early_stop=True, want_post=True)
-    b = code.decode(x, max_iters=8, alpha=0.75, normalise=True, early_stop=True, want_post=True)
+    b = code.decode(x, max_iters=8, alpha=alpha, normalise=normalise, early_stop=True,
+                    want_post=True)
     for u, v in zip(a, b):
         assert torch.equal(u, v)
 
@@ -80,7 +84,7 @@ def test_learned_dynamic_handout(ldpc, request):
     shape = synth.wifi_n648_r12()
     rc, _, llr = _inputs(shape, 150, 1.5, frame0=77)
     w = _weights(rc, 8, 3)
-    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, 8, early_stop=True)
+    wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=8, early_stop=True)
     code = ldpc.Code(shape.hbm, shape.z)
     gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
                                      early_stop=True, want_post=True)
@@ -98,7 +102,7 @@ def test_learned_fallback_pipeline(ldpc, shape, T, ebn0):
     frames = 301
     rc, _, llr = _inputs(shape, frames, ebn0)
     w = _weights(rc, T, 11, 0.6, 0.9)
-    wh, wi, _ = rc.decode_layered_weighted_f32(llr, w, T, early_stop=True, want_post=False)
+    wh, wi, _ = rc.decode_learned_f32(llr, w, max_iters=T, early_stop=True, want_post=False)
     bits = oracle.unpack_hard(wh, rc.n)
     fail = np.array([rc.syndrome_weight(b) != 0 for b in bits])
     assert 0 < fail.sum() < frames

@@ -69,7 +69,7 @@ def test_largest_code_bit_exact(ldpc):
                              normalise=True, early_stop=True, want_post=True)
     assert (gi.cpu().numpy() == wi).all() and (gp.cpu().numpy() == wp).all()
     w = np.random.default_rng(1).uniform(0.5, 1.0, (5, rc.nnz_blocks)).astype(np.float32)
-    wh, wi, wp = rc.decode_layered_weighted_f32(llr, w, 5, early_stop=True)
+    wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=5, early_stop=True)
     gh, gi, gp = code.decode_learned(x, torch.from_numpy(w).cuda(), early_stop=True,
                                      want_post=True)
     assert (gi.cpu().numpy() == wi).all() and (gp.cpu().numpy() == wp).all()

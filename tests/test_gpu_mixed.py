@@ -176,7 +176,7 @@ def test_mixed_learned_and_fallback(ldpc):
             continue
         rc = oracle.RefCode(s.hbm, s.z)
         x = np.stack([llr_h[plan.llr_off[f]:plan.llr_off[f] + rc.n] for f in idx])
-        h, i, p = rc.decode_layered_weighted_f32(x, ws[ci], Ts[ci], early_stop=True)
+        h, i, p = rc.decode_learned_f32(x, ws[ci], max_iters=Ts[ci], early_stop=True)
         bits = oracle.unpack_hard(h, rc.n)
         bad = np.array([rc.syndrome_weight(b) != 0 for b in bits])
         bad_total += int(bad.sum())

@@ -68,8 +68,13 @@ def test_forward_checkpoints_bit_exact(ldpc, shape, T, frames):
     x, b, wt = _cuda(llr, cw, w)
     post, rows, loss, loss_sum = code.train_forward(x, b, wt, 0.5)
     assert (post.cpu().numpy() == posts.numpy()).all()
+    # inference applies the weights with fused updates (the oracle's learned
+    # decoder); training rounds w m first (the weighted decoder)
     _, _, p_inf = code.decode_learned(x, wt, early_stop=False, want_post=True)
-    assert torch.equal(p_inf, post[-1])
+    _, _, p_ref = rc.decode_learned_f32(llr, w, max_iters=T, early_stop=False)
+    assert (p_inf.cpu().numpy() == p_ref).all()
+    _, _, p_w = rc.decode_layered_weighted_f32(llr, w, T, early_stop=False)
+    assert (post[-1].cpu().numpy() == p_w).all()
     # loss: the float64 cross-entropy of the same posteriors
     want = learned.bce_posterior(posts.double(), torch.from_numpy(cw).double()).sum(dim=(0, 2))
     np.testing.assert_allclose(loss.cpu().numpy(), want.numpy(), rtol=1e-5)
