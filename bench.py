@@ -555,9 +555,16 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     nf = F * ws
     eb = _mixed_ebn0(ldpc, torch, plan, codes, first, LEARNED_EBN0)
     errs = {}
+    tuned = {}
     for name in names:
         if name in weights_of:
             plan.set_weights(weights_of[name])   # outside the timed region
+        if name == "learned":
+            # the learned launches share the FP32 items and caps: tune them on
+            # the gated learned decoder (plain FP32-20 was timed with its own)
+            t1 = time.time()
+            plan.autotune_learned(batch.llr, reps=2, out=outs["learned_gated"], **gate)
+            tuned = {"seconds": time.time() - t1, "groups": plan.groups()}
         for _ in range(2):
             run(name)
         barrier()
@@ -618,7 +625,7 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
                                         "the recipe's common [1, 4] dB",
                "ablation_range_20": "operating-range weights, up to 20 iterations, no "
                                     "checkpoints"},
-           "weights_per_iteration": wstat,
+           "weights_per_iteration": wstat, "learned_autotune": tuned,
            "training": {"per_code": {"steps": args.scale_train_steps, "batch": 1024, "lr": 2e-3,
                                      "T": "8 (R <= 2/3), 6 (R > 2/3)",
                                      "operating_range": "[b, max(b + 1, 4.5)] dB, b the lowest "
@@ -1098,7 +1105,7 @@ def main():
     roofline = {"bound": "alu", "achieved": ach_tops, "peak": peak_tops, "unit": "Tops/s",
                 "frac": ach_tops / peak_tops,
                 "traffic": _profile_traffic("ldpc_decode_i8_wifi1944"),
-                "kernel": "decode_i8_kernel<20> (int8, four frames per word)",
+                "kernel": "decode_i8_kernel<20, 19> (int8, four frames per word; 19 edge slots, the code's largest row degree)",
                 "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz "
                               "(median SM clock sampled during the timed region)",
                 "hbm_gbs": (len(EBN0) * ((F + 3) // 4) * code.n * 4 +

@@ -445,6 +445,14 @@ ldpc_status ldpc_decode_mixed_learned_ex(ldpc_mixed_plan *plan, const float *d_l
                                          const ldpc_learned_params *lp, uint32_t *d_hard,
                                          int32_t *d_iters, float *d_post, cudaStream_t stream);
 
+/* ldpc_mixed_autotune for the learned decoder: the learned launches share
+ * the FP32 launches' work items, residency caps and concurrency; this tunes
+ * them by timing ldpc_decode_mixed_learned_ex with `lp` (so the FP32 plain
+ * decoder runs with them afterwards too).  Needs ldpc_mixed_set_weights. */
+ldpc_status ldpc_mixed_autotune_learned(ldpc_mixed_plan *plan, const float *d_llr,
+                                        const ldpc_learned_params *lp, uint32_t *d_hard,
+                                        int32_t *d_iters, int reps, cudaStream_t stream);
+
 /* d_bad uint8[frames]: 1 where a frame's hard decisions (plan layout)
  * violate a parity check (eq. 21 termination test), else 0. */
 ldpc_status ldpc_mixed_frame_flags(const ldpc_mixed_plan *plan, const uint32_t *d_hard,

@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False):
         "ldpc_decode_learned_minsum_ex": ([vp, vp, i64, vp, i32, P(_LearnedParams), vp, vp, vp,
                                            vp], i32),
         "ldpc_decode_mixed_learned_ex": ([vp, vp, P(_LearnedParams), vp, vp, vp, vp], i32),
+        "ldpc_mixed_autotune_learned": ([vp, vp, P(_LearnedParams), vp, vp, i32, vp], i32),
         "ldpc_learned_fallback_workspace_bytes": ([vp, i64], sz),
         "ldpc_decode_learned_fallback": ([vp, vp, i64, vp, i32, P(_Params), f32, i32, vp, vp,
                                           P(i64), vp, sz, vp], i32),
@@ -567,6 +568,17 @@ class MixedPlan:
                                                        _ptr(hard), _ptr(iters), _ptr(post),
                                                        _stream(stream)))
         return hard, iters, post
+
+    def autotune_learned(self, llr, max_iters: int = 0, stop_iter=(0, 0), stop_frac=(0.0, 0.0),
+                         reps: int = 3, out=None, stream=None):
+        """Tune the work items, residency caps and concurrency the learned
+        (and FP32) launches share, timing the learned decoder."""
+        hard, iters = out if out is not None else self.empty_outputs()
+        lp = _learned_params(max_iters, True, stop_iter, stop_frac)
+        _check(load().ldpc_mixed_autotune_learned(self._h, _ptr(llr), ctypes.byref(lp),
+                                                  _ptr(hard), _ptr(iters), int(reps),
+                                                  _stream(stream)))
+        return self.groups()
 
     def frame_flags(self, hard, out=None, stream=None):
         torch = _torch()

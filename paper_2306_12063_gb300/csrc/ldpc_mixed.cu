@@ -942,19 +942,14 @@ ldpc_status ldpc_mixed_stats(const ldpc_mixed_plan *plan, const uint8_t *d_info,
                        stream);
 }
 
-ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const void *d_in,
-                                const ldpc_decode_params *params, uint32_t *d_hard,
-                                int32_t *d_iters, int reps, cudaStream_t stream) {
-    if (!plan) return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_autotune: plan is NULL");
-    ldpc_status st = check_params(params, dtype, "ldpc_mixed_autotune");
-    if (st != LDPC_OK) return st;
-    MixedPlan &p = *plan->p;
-    if (p.frames == 0) return LDPC_OK;
-    if (!d_in || !d_hard || !d_iters || reps < 1 || reps > 100)
-        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_autotune: NULL buffer or reps");
-    if ((st = bind_plan(p)) != LDPC_OK) return st;
-    const int dt = dtype == LDPC_F32 ? 0 : 1;
-    const DecodeParams dp = to_params(params);
+// Autotuner body.  lt: the launch type (0 FP32, 1 int8, 2 learned FP32);
+// the learned launches use the FP32 work items, residency caps and
+// concurrency, so lt = 2 tunes those (timing the learned decoder).
+static ldpc_status autotune_impl(MixedPlan &p, int lt, const void *d_in, const DecodeParams &dp,
+                                 uint32_t *d_hard, int32_t *d_iters, int reps,
+                                 cudaStream_t stream) {
+    const int dt = lt == 1 ? 1 : 0;   // the tuned slot
+    ldpc_status st = LDPC_OK;
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -964,7 +959,7 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
         std::vector<float> t;
         for (int r = 0; r < reps; ++r) {
             cudaEventRecord(a, stream);
-            ldpc_status s2 = launch_all(p, dt, d_in, dp, d_hard, d_iters, nullptr, stream);
+            ldpc_status s2 = launch_all(p, lt, d_in, dp, d_hard, d_iters, nullptr, stream);
             if (s2 != LDPC_OK) return s2;
             cudaEventRecord(b, stream);
             cudaError_t e2 = cudaEventSynchronize(b);
@@ -984,7 +979,7 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
         std::vector<float> t;
         for (int r = 0; r < reps; ++r) {
             cudaEventRecord(a, stream);
-            ldpc_status s2 = launch_group(p, gi, dt, d_in, dp, d_hard, d_iters, nullptr, stream);
+            ldpc_status s2 = launch_group(p, gi, lt, d_in, dp, d_hard, d_iters, nullptr, stream);
             if (s2 != LDPC_OK) return s2;
             cudaEventRecord(b, stream);
             cudaError_t e2 = cudaEventSynchronize(b);
@@ -999,7 +994,7 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
     };
     const std::vector<int> chunks = dt == 0 ? std::vector<int>{1, 2, 4, 8, 16, 32}
                                             : std::vector<int>{4, 8, 16, 32, 64, 128};
-    st = launch_all(p, dt, d_in, dp, d_hard, d_iters, nullptr, stream);   // warm-up
+    st = launch_all(p, lt, d_in, dp, d_hard, d_iters, nullptr, stream);   // warm-up
     // each group's chunk, timed on the group alone
     for (size_t gi = 0; st == LDPC_OK && gi < p.groups.size(); ++gi) {
         MixedGroup &g = p.groups[gi];
@@ -1055,6 +1050,39 @@ ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const v
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return st;
+}
+
+ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const void *d_in,
+                                const ldpc_decode_params *params, uint32_t *d_hard,
+                                int32_t *d_iters, int reps, cudaStream_t stream) {
+    if (!plan) return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_autotune: plan is NULL");
+    ldpc_status st = check_params(params, dtype, "ldpc_mixed_autotune");
+    if (st != LDPC_OK) return st;
+    MixedPlan &p = *plan->p;
+    if (p.frames == 0) return LDPC_OK;
+    if (!d_in || !d_hard || !d_iters || reps < 1 || reps > 100)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_autotune: NULL buffer or reps");
+    if ((st = bind_plan(p)) != LDPC_OK) return st;
+    return autotune_impl(p, dtype == LDPC_F32 ? 0 : 1, d_in, to_params(params), d_hard, d_iters,
+                         reps, stream);
+}
+
+ldpc_status ldpc_mixed_autotune_learned(ldpc_mixed_plan *plan, const float *d_llr,
+                                        const ldpc_learned_params *lp, uint32_t *d_hard,
+                                        int32_t *d_iters, int reps, cudaStream_t stream) {
+    const char *who = "ldpc_mixed_autotune_learned";
+    if (!plan || !lp) return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": NULL argument");
+    DecodeParams dp;
+    ldpc_status st = learned_run_params(lp, &dp, who);
+    if (st) return st;
+    MixedPlan &p = *plan->p;
+    if (p.frames == 0) return LDPC_OK;
+    if (!p.d_wptr)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": no weights (ldpc_mixed_set_weights)");
+    if (!d_llr || !d_hard || !d_iters || reps < 1 || reps > 100)
+        return fail(LDPC_ERR_INVALID_ARG, std::string(who) + ": NULL buffer or reps");
+    if ((st = bind_plan(p)) != LDPC_OK) return st;
+    return autotune_impl(p, 2, d_llr, dp, d_hard, d_iters, reps, stream);
 }
 
 ldpc_status ldpc_mixed_graph_create(ldpc_mixed_plan *plan, ldpc_dtype dtype, const float *d_llr,

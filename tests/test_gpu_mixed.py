@@ -239,3 +239,8 @@ def test_mixed_learned_past_table_with_checkpoints(ldpc):
             assert it[f] == i[j] and (hw[a:b] == h[j]).all()
             assert (pw[plan.llr_off[f]:plan.llr_off[f + 1]] == p[j]).all()
     assert stopped > 0 and it.max() > max(Ts)
+    # tuning the launches for the learned decoder changes the schedule only
+    plan.autotune_learned(batch.llr, max_iters=16, stop_iter=si, stop_frac=sf, reps=1)
+    h2, i2, p2 = plan.decode_learned(batch.llr, want_post=True, max_iters=16, stop_iter=si,
+                                     stop_frac=sf)
+    assert torch.equal(h2, hard) and torch.equal(i2, iters) and torch.equal(p2, post)
