@@ -409,6 +409,10 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
                      "per_code_launches": {"value": info_bits * ws / (pc_ms * 1e-3) / 1e9,
                                            "ms": pc_ms, "launches": len(per_code)},
                      "alg_tops": ops / (direct_ms * 1e-3) / 1e12,
+                     "alg_frac": ops / (direct_ms * 1e-3) / (SMS * LANES_PER_SM * 2070e6),
+                     "alg_unit": ("word-operations (four frames)" if dt == ldpc.I8X4
+                                  else "operations (one frame)") + " per second; alg_frac "
+                                 f"against {SMS} SMs x {LANES_PER_SM} lanes x 2070 MHz",
                      "fer": float(st[1]) / nf, "mean_iters": it_sum / nf,
                      "autotune_seconds": tune_s, "groups": groups,
                      "serial_groups": plan.serial()[name]}
