@@ -70,14 +70,19 @@ __global__ void __launch_bounds__(32)
     __syncwarp();
     uint32_t phase = 0;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
-    int64_t f = blockIdx.x * static_cast<int64_t>(W) + warp;   // first frame static,
-    while (f < frames) {                                       // the rest from the counter
+    // the first frame static, the rest from the counter, each drawn one frame
+    // ahead so that its LLRs are pulled into L2 while this one decodes
+    int64_t f = blockIdx.x * static_cast<int64_t>(W) + warp;
+    int64_t pend = f < frames ? next_work(work, nwarps, lane) : frames;
+    while (f < frames) {
+        if (pend < frames) prefetch_l2(llr + pend * c.n, 4u * static_cast<uint32_t>(c.n), lane);
         const int done = decode_one_f32<DMAX, WT, DM>(c, Zs, rows, wbuf, llr + f * c.n,
                                                       use_bulk != 0, bar, phase, p, lane);
         if (!done) return;
         write_frame_f32(c, Zs, f, done, hard, iters, post, lane);
         __syncwarp();
-        f = next_work(work, nwarps, lane);
+        f = pend;
+        if (f < frames) pend = next_work(work, nwarps, lane);
     }
 }
 
@@ -124,6 +129,10 @@ __global__ void __launch_bounds__(32)
         __syncwarp();
     }
     const int64_t dyn_base = 4 * nwarps;   // frames beyond the initial groups
+    // the next refill's frame, drawn one refill ahead so that its packed row
+    // is pulled into L2 while the word keeps iterating
+    int64_t pend = next_work(work, dyn_base, lane);
+    if (pend < frames) prefetch_l2(llr + (pend >> 2) * c.n, 4u * static_cast<uint32_t>(c.n), lane);
     for (;;) {
         bool any = false;
         for (int b = 0; b < 4; ++b) any |= fr[b] >= 0;
@@ -140,11 +149,14 @@ __global__ void __launch_bounds__(32)
             if (!ok && kb[b] < p.max_iters) continue;
             // frame finished at this iteration: outputs now, then refill the byte
             write_frame_i8(c, Zs, fr[b], b, kb[b], hard, iters, post, lane);
-            const int64_t nf = next_work(work, dyn_base, lane);
+            const int64_t nf = pend;
             if (nf >= frames) {
                 fr[b] = -1;
                 continue;
             }
+            pend = next_work(work, dyn_base, lane);
+            if (pend < frames)
+                prefetch_l2(llr + (pend >> 2) * c.n, 4u * static_cast<uint32_t>(c.n), lane);
             fr[b] = nf;
             kb[b] = 0;
             const uint32_t *src = llr + (nf >> 2) * c.n;

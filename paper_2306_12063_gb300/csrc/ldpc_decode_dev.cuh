@@ -586,6 +586,14 @@ __device__ __forceinline__ bool stage_bulk(const DevCode &c, uint32_t *Zs, const
     return true;
 }
 
+// Pulls `bytes` bytes at p into L2 ahead of their use (one prefetch per
+// 128-byte line, spread over the lanes; no data is returned).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes, int lane) {
+    const char *c = static_cast<const char *>(p);
+    for (uint32_t o = static_cast<uint32_t>(lane) * 128u; o < bytes; o += 32u * 128u)
+        asm volatile("prefetch.L2 [%0];" ::"l"(c + o));
+}
+
 __device__ __forceinline__ int64_t next_work(unsigned long long *ctr, int64_t base, int lane) {
     unsigned long long v = 0;
     if (lane == 0) v = atomicAdd(ctr, 1ull);

@@ -75,6 +75,11 @@ __global__ void __launch_bounds__(32)
         for (long long i = item.start; i < item.start + item.count; ++i) {
             const long long uf = uframe[i];
             if (uf < 0) continue;   // padding of the code's range
+            // the item's next frame into L2 while this one decodes
+            if (i + 1 < item.start + item.count) {
+                const long long un = uframe[i + 1];
+                if (un >= 0) prefetch_l2(llr + llr_off[un], 4u * static_cast<uint32_t>(c.n), lane);
+            }
             const float *src = llr + llr_off[uf];
             const int done = decode_one_f32<DMAX, WT>(
                 c, Zs, rows, wbuf, reinterpret_cast<const uint32_t *>(src), use_bulk != 0,
@@ -187,6 +192,10 @@ __global__ void __launch_bounds__(32, 12)
                 kb[b] = 0;
                 const long long li = nf - base;
                 const uint32_t *src = qc + (li >> 2) * c.n;
+                // the following refill's packed row into L2
+                if (next < end && ((next - base) >> 2) != (li >> 2))
+                    prefetch_l2(qc + ((next - base) >> 2) * c.n, 4u * static_cast<uint32_t>(c.n),
+                                lane);
                 const uint32_t sel = (0x3210u & ~(0xFu << (4 * b))) |
                                      (static_cast<uint32_t>(4 + (li & 3)) << (4 * b));
                 __syncwarp();

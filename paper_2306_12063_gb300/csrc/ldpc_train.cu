@@ -52,9 +52,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // One check row of one layer, iteration t: eq. 22 for every edge, the two
 // smallest |Z_mn| and the sign product, then eq. 23 (weighted) and eq. 20.
-// The rounding matches the learned inference decoder step for step, so both
-// produce the same posteriors.  Q and v receive Z_mn and the variable of
-// each edge; returns the row's new state.
+// The rounding is that of the oracle's weighted decoder: w m is rounded,
+// then added or subtracted (the learned inference decoder fuses the two, so
+// its posteriors differ from these by rounding only).  Q and v receive Z_mn
+// and the variable of each edge; returns the row's new state.
 template <int DMAX>
 __device__ __forceinline__ uint4 row_forward(const DevCode &c, int e0, int d, int r, float *Zs,
                                              uint4 st, const float *wprev, const float *wcur,
