@@ -407,8 +407,10 @@ ldpc_status ldpc_mixed_stats(const ldpc_mixed_plan *plan, const uint8_t *d_info,
 /* Autotuner: for each launch group in turn, picks the frames per work item
  * (FP32 1..32, int8 4..128) and then a resident-block cap per SM (none, 16,
  * 8, 4) that minimise the median time of `reps` decodes of this batch, the
- * other groups' choices held fixed.  Runs and synchronises `stream`; the
- * choices stay in the plan (ldpc_mixed_group_info reports them). */
+ * other groups' choices held fixed; for FP32 then the warps per frame (1..3)
+ * and frames per block (1, 2, 4) of each group, and finally concurrent or
+ * serial groups.  Runs and synchronises `stream`; the choices stay in the
+ * plan (ldpc_mixed_group_launch and ldpc_mixed_group_info report them). */
 ldpc_status ldpc_mixed_autotune(ldpc_mixed_plan *plan, ldpc_dtype dtype, const void *d_in,
                                 const ldpc_decode_params *params, uint32_t *d_hard,
                                 int32_t *d_iters, int reps, cudaStream_t stream);
@@ -452,6 +454,27 @@ ldpc_status ldpc_decode_mixed_learned_ex(ldpc_mixed_plan *plan, const float *d_l
 ldpc_status ldpc_mixed_autotune_learned(ldpc_mixed_plan *plan, const float *d_llr,
                                         const ldpc_learned_params *lp, uint32_t *d_hard,
                                         int32_t *d_iters, int reps, cudaStream_t stream);
+
+/* Launch settings of one launch group (not in the paper: tuning of the
+ * batched decoders).  frames_per_item: frames per work item taken from the
+ * group's counter; blocks_per_sm: resident blocks per SM, 0 = as many as fit;
+ * warps_per_frame (FP32, 1..3): warps that decode one frame together, each
+ * taking every warps_per_frame-th round of a layer's rows, with a barrier
+ * between layers; frames_per_block (FP32, 1..4): such teams per block.  The
+ * int8 launches use 1 and 1.  The FP32 settings also serve the learned
+ * launches. */
+typedef struct {
+    int frames_per_item;
+    int blocks_per_sm;
+    int warps_per_frame;
+    int frames_per_block;
+} ldpc_group_launch;
+
+/* Reads (get) and/or replaces (set) the settings of `group` for `dtype`;
+ * either pointer may be NULL.  ldpc_mixed_autotune searches the same
+ * settings.  Results do not depend on them. */
+ldpc_status ldpc_mixed_group_launch(ldpc_mixed_plan *plan, int group, ldpc_dtype dtype,
+                                    const ldpc_group_launch *set, ldpc_group_launch *get);
 
 /* d_bad uint8[frames]: 1 where a frame's hard decisions (plan layout)
  * violate a parity check (eq. 21 termination test), else 0. */

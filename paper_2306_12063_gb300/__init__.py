@@ -39,6 +39,11 @@ class _Params(ctypes.Structure):
                 ("normalise", ctypes.c_int), ("early_stop", ctypes.c_int)]
 
 
+class _GroupLaunch(ctypes.Structure):
+    _fields_ = [("frames_per_item", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("warps_per_frame", ctypes.c_int), ("frames_per_block", ctypes.c_int)]
+
+
 class _LearnedParams(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("early_stop", ctypes.c_int),
                 ("stop_iter", ctypes.c_int * 2), ("stop_frac", ctypes.c_float * 2)]
@@ -101,6 +106,7 @@ def load(build_if_missing: bool = False):
                                            vp], i32),
         "ldpc_decode_mixed_learned_ex": ([vp, vp, P(_LearnedParams), vp, vp, vp, vp], i32),
         "ldpc_mixed_autotune_learned": ([vp, vp, P(_LearnedParams), vp, vp, i32, vp], i32),
+        "ldpc_mixed_group_launch": ([vp, i32, i32, P(_GroupLaunch), P(_GroupLaunch)], i32),
         "ldpc_learned_fallback_workspace_bytes": ([vp, i64], sz),
         "ldpc_decode_learned_fallback": ([vp, vp, i64, vp, i32, P(_Params), f32, i32, vp, vp,
                                           P(i64), vp, sz, vp], i32),
@@ -473,8 +479,30 @@ class MixedPlan:
             _check(load().ldpc_mixed_group_info(self._h, g, *[ctypes.byref(x) for x in v]))
             keys = ("slot_class", "codes", "smem_f32", "smem_i8", "chunk_f32", "chunk_i8",
                     "blocks_per_sm_f32", "blocks_per_sm_i8")
-            out.append(dict(zip(keys, [x.value for x in v])))
+            d = dict(zip(keys, [x.value for x in v]))
+            t = _GroupLaunch()
+            _check(load().ldpc_mixed_group_launch(self._h, g, F32, None, ctypes.byref(t)))
+            d["warps_per_frame_f32"] = t.warps_per_frame
+            d["frames_per_block_f32"] = t.frames_per_block
+            out.append(d)
         return out
+
+    def group_launch(self, group: int, dtype: int = F32, frames_per_item=None,
+                     blocks_per_sm=None, warps_per_frame=None, frames_per_block=None):
+        """The launch settings of one group (ldpc_group_launch as a dict);
+        any argument given replaces that setting first."""
+        cur = _GroupLaunch()
+        _check(load().ldpc_mixed_group_launch(self._h, int(group), int(dtype), None,
+                                              ctypes.byref(cur)))
+        new = {"frames_per_item": frames_per_item, "blocks_per_sm": blocks_per_sm,
+               "warps_per_frame": warps_per_frame, "frames_per_block": frames_per_block}
+        if any(v is not None for v in new.values()):
+            for k, v in new.items():
+                if v is not None:
+                    setattr(cur, k, int(v))
+            _check(load().ldpc_mixed_group_launch(self._h, int(group), int(dtype),
+                                                  ctypes.byref(cur), ctypes.byref(cur)))
+        return {k: getattr(cur, k) for k, _ in _GroupLaunch._fields_}
 
     def serial(self):
         a, b = ctypes.c_int(), ctypes.c_int()

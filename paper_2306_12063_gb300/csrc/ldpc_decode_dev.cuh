@@ -134,11 +134,14 @@ __device__ __forceinline__ uint32_t scale34(uint32_t m) {
 // does.
 __host__ __device__ constexpr int wpad(int dmax) { return (dmax + 3) & ~3; }
 
+// t0, tstep: the row slots t = t0, t0 + tstep, ... of the layer this warp
+// processes (a team of tstep warps shares a frame's rows; 0, 1 for one warp).
 template <int DS, int DMAX, bool WT = false>
 __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, uint32_t *Zs,
                                           uint32_t *rows, int lane, bool norm, float alpha,
                                           const float *wprev = nullptr,
-                                          const float *wcur = nullptr) {
+                                          const float *wcur = nullptr, int t0 = 0,
+                                          int tstep = 1) {
     (void)d;   // leading unused slots run like the others (see the store below)
     float wp[WT ? wpad(DMAX) : 1], wc[WT ? wpad(DMAX) : 1];
     if (WT) {
@@ -154,7 +157,7 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
             wc[WT ? 4 * j + 2 : 0] = b.z; wc[WT ? 4 * j + 3 : 0] = b.w;
         }
     }
-    for (int t = 0; t < c.rpl; ++t) {
+    for (int t = t0; t < c.rpl; t += tstep) {
         const int r = lane + 32 * t;
         if (r >= c.z) break;
         uint32_t *rs = rows + (layer * c.z + r) * kRowWordsF32;
@@ -306,15 +309,16 @@ template <int DS, bool WT = false, int DM = DS>
 __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint32_t *Zs,
                                               uint32_t *rows, int lane, bool norm, float alpha,
                                               const float *wprev = nullptr,
-                                              const float *wcur = nullptr) {
+                                              const float *wcur = nullptr, int t0 = 0,
+                                              int tstep = 1) {
     static_assert(!WT || ((DS - DM) % 4 == 0 && (DS - small_slots<DS, DM>()) % 4 == 0),
                   "learned weights need 16-byte aligned slot offsets");
     const int d = __ldg(c.rowinfo + layer) & 255;
     if (use_sub<DS, DM>(d))
         layer_f32<DS, small_slots<DS, DM>(), WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev,
-                                                 wcur);
+                                                 wcur, t0, tstep);
     else
-        layer_f32<DS, DM, WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur);
+        layer_f32<DS, DM, WT>(c, layer, d, Zs, rows, lane, norm, alpha, wprev, wcur, t0, tstep);
 }
 
 // ---------------------------------------------------------------------------
@@ -655,6 +659,108 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
                 return k;
         } else if (p.early_stop && syndrome_ok_f32<DMAX, DM>(c, Zs, lane)) {
             return k;
+        }
+    }
+    return p.max_iters;
+}
+
+// ---------------------------------------------------------------------------
+// Teams: tstep warps decoding one FP32 frame together, warp wi taking the row
+// slots t = wi, wi + tstep, ... of every layer, with a named barrier between
+// layers.  Every decision (copy timeout, stop, the next work item) goes
+// through the team's shared words tw[] so that all warps of a team take the
+// same path and meet at every barrier.  tw[0]: copy-timeout flag; tw[1 + w]:
+// warp w's syndrome result; tw[4..5]: the next work item.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void team_sync(int id, int nw) {
+    if (nw == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nw * 32) : "memory");
+}
+
+// This warp's part of the syndrome: bit 31 set (warp-uniform) when one of
+// its rows fails, or (count) the number of its failing rows.
+template <int DS, int DM>
+__device__ __forceinline__ uint32_t syndrome_part_f32(const DevCode &c, const uint32_t *Zs, int lane,
+                                                      int t0, int tstep, bool count) {
+    uint32_t acc = 0;
+    for (int l = 0; l < c.mb; ++l) {
+        const int d = __ldg(c.rowinfo + l) & 255;
+        for (int t = t0; t < c.rpl; t += tstep) {
+            if (lane + 32 * t >= c.z) break;
+            const uint32_t par = use_sub<DS, DM>(d)
+                                     ? syndrome_row_f32<DS, small_slots<DS, DM>()>(c, Zs, l, t, lane)
+                                     : syndrome_row_f32<DS, DM>(c, Zs, l, t, lane);
+            acc = count ? acc + (par >> 31) : (acc | par);
+        }
+    }
+    return count ? __reduce_add_sync(kFull, acc) : (__any_sync(kFull, acc >> 31) ? 1u : 0u);
+}
+
+// decode_one_f32 for a team of tstep warps (wi: this warp's index in it).
+template <int DMAX, bool WT>
+__device__ __forceinline__ int decode_one_f32_team(const DevCode &c, uint32_t *Zs, uint32_t *rows,
+                                                   float *wbuf, const uint32_t *src,
+                                                   bool use_bulk, uint64_t *bar, uint32_t &phase,
+                                                   const DecodeParams &p, int lane, int wi,
+                                                   int tstep, int bar_id, volatile int *tw) {
+    const int tid = wi * 32 + lane, nthr = tstep * 32;
+    fence_proxy_async_smem();
+    if (tid == 0) tw[0] = 0;
+    team_sync(bar_id, tstep);   // the previous frame's reads of Zs are done
+    if (use_bulk) {
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(c.n) * 4u);
+            bulk_copy_g2s(Zs, src, static_cast<uint32_t>(c.n) * 4u, bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, phase, kWaitLimit);
+        if (!__all_sync(kFull, ok)) {
+            if (lane == 0) {
+                atomicOr(c.status, kStatusCopyTimeout);
+                tw[0] = 1;
+            }
+            mbar_wait_bounded(bar, phase, kWaitLimit);   // let the copy land
+        }
+        team_sync(bar_id, tstep);
+        if (tw[0]) return 0;
+        phase ^= 1u;
+    } else {
+        for (int i = tid; i < c.n; i += nthr) Zs[i] = __ldg(src + i);
+    }
+    for (int i = tid; i < c.m * kRowWordsF32; i += nthr) rows[i] = 0u;   // all L_mn = 0
+    team_sync(bar_id, tstep);
+    const bool norm = p.normalise != 0;
+    const int wT = p.weight_iters > 0 ? p.weight_iters : p.max_iters;
+    const bool checkpoints = p.early_stop && (p.stop_iter[0] | p.stop_iter[1]) != 0;
+    const int lim0 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[0], static_cast<float>(c.m))));
+    const int lim1 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[1], static_cast<float>(c.m))));
+    for (int k = 1; k <= p.max_iters; ++k) {
+        constexpr int WP = wpad(DMAX);
+        float *wcur = wbuf + (k & 1) * c.mb * WP;
+        const float *wprev = k > 1 ? wbuf + ((k - 1) & 1) * c.mb * WP : wcur;
+        if (WT && k <= wT + 1) {
+            const float *wk = p.weights + static_cast<size_t>(min(k, wT) - 1) * p.n_edges;
+            for (int i = tid; i < c.mb * WP; i += nthr) {
+                const int g = __ldg(c.wgather + i);
+                wcur[i] = g >= 0 ? __ldg(wk + g) : 0.0f;
+            }
+            team_sync(bar_id, tstep);
+        }
+        for (int l = 0; l < c.mb; ++l) {
+            layer_f32_any<DMAX, WT>(c, l, Zs, rows, lane, norm, p.alpha, wprev + l * WP,
+                                    wcur + l * WP, wi, tstep);
+            team_sync(bar_id, tstep);
+        }
+        if (p.early_stop) {
+            const uint32_t part = syndrome_part_f32<DMAX, DMAX>(c, Zs, lane, wi, tstep, checkpoints);
+            if (lane == 0) tw[1 + wi] = static_cast<int>(part);
+            team_sync(bar_id, tstep);
+            int u = 0;
+            for (int w = 0; w < tstep; ++w) u += tw[1 + w];
+            if (u == 0 || (checkpoints && ((k == p.stop_iter[0] && u > lim0) ||
+                                           (k == p.stop_iter[1] && u > lim1))))
+                return k;
         }
     }
     return p.max_iters;

@@ -93,6 +93,77 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// The FP32 launch with teams: fpb teams per block, each of wpf warps decoding
+// one frame at a time (warps per frame and frames per CTA, both tuned per
+// launch group).  Team g's shared memory is its own region of team_words
+// words (the one-warp layout, then the team's eight shared words); its
+// warps meet at named barrier 1 + g.  A team's first work item is static,
+// the rest come from the group's counter through its leader.
+template <int DMAX, bool WT = false>
+__global__ void __launch_bounds__(32 * 12)
+    mixed_f32_team_kernel(const DevCode *__restrict__ codes, const MixedItem *__restrict__ items,
+                          int n_items, const long long *__restrict__ uframe,
+                          const long long *__restrict__ llr_off,
+                          const long long *__restrict__ hard_off, const float *__restrict__ llr,
+                          DecodeParams p, uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
+                          float *__restrict__ post, unsigned long long *work, int use_bulk,
+                          const float *const *wptr, const int *wT, int wpf, int fpb,
+                          int team_words) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp / wpf, wi = warp - g * wpf;
+    uint32_t *base = smem + static_cast<size_t>(g) * team_words;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base);
+    uint32_t *Zs = base + 4;
+    volatile int *tw = reinterpret_cast<volatile int *>(base + team_words - 8);
+    const int bar_id = 1 + g;
+    if (use_bulk && wi == 0 && lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    team_sync(bar_id, wpf);
+    uint32_t phase = 0;
+    long long it = static_cast<long long>(blockIdx.x) * fpb + g;
+    while (it < n_items) {
+        const MixedItem item = items[it];
+        const DevCode c = codes[item.code];
+        uint32_t *rows = Zs + posterior_words(c.n);
+        float *wbuf = reinterpret_cast<float *>(rows + ((c.m * 3 + 3) & ~3));
+        DecodeParams pc = p;
+        if (WT) {
+            pc.weights = wptr[item.code];
+            pc.weight_iters = wT[item.code];
+            pc.max_iters = p.max_iters > 0 ? p.max_iters : wT[item.code];
+            pc.n_edges = c.n_edges;
+        }
+        if (wi == 0) Zs[c.n + lane] = 0x7F800000u;   // dummy posterior of unused edge slots
+        for (long long i = item.start; i < item.start + item.count; ++i) {
+            const long long uf = uframe[i];
+            if (uf < 0) continue;   // padding of the code's range
+            if (i + 1 < item.start + item.count && wi == 0) {
+                const long long un = uframe[i + 1];
+                if (un >= 0) prefetch_l2(llr + llr_off[un], 4u * static_cast<uint32_t>(c.n), lane);
+            }
+            const float *src = llr + llr_off[uf];
+            const int done = decode_one_f32_team<DMAX, WT>(
+                c, Zs, rows, wbuf, reinterpret_cast<const uint32_t *>(src), use_bulk != 0, bar,
+                phase, pc, lane, wi, wpf, bar_id, tw);
+            if (!done) return;   // team-uniform
+            if (wi == 0)
+                write_frame_f32_to(c, Zs, done, hard + hard_off[uf], iters + uf,
+                                   post ? post + llr_off[uf] : nullptr, lane);
+        }
+        team_sync(bar_id, wpf);   // outputs written, tw[4..5] free
+        if (wi == 0 && lane == 0) {
+            const long long nx = static_cast<long long>(atomicAdd(work, 1ull)) +
+                                 static_cast<long long>(gridDim.x) * fpb;
+            *reinterpret_cast<volatile long long *>(tw + 4) = nx;
+        }
+        team_sync(bar_id, wpf);
+        it = *reinterpret_cast<volatile long long *>(tw + 4);
+    }
+}
+
 // One int8 launch: a work item's frames enter a packed word four at a time
 // and each byte lane is refilled as soon as its frame stops (as in the
 // single-code kernel), from the item's remaining frames and then from the
@@ -378,6 +449,8 @@ struct MixedGroup {
     int smem_learned = 0;                // FP32 plus two iterations of staged weights
     int chunk[2] = {8, 16};              // frames per work item
     int per_sm[2] = {0, 0};              // resident blocks per SM (0: occupancy limit)
+    int wpf = 1;                         // FP32 warps per frame (a team shares the rows)
+    int fpb = 1;                         // FP32 frames (teams) per block
     MixedItem *d_items[2] = {nullptr, nullptr};
     int n_items[2] = {0, 0};
     int built_chunk[2] = {0, 0};         // chunk the item list was built for
@@ -486,24 +559,53 @@ static ldpc_status launch_group_t(MixedPlan &pl, MixedGroup &g, int gi, int dt, 
                                   void *d_post, cudaStream_t s) {
     const bool learned = dt == 2;
     if (learned) dt = 0;
-    const int smem = learned ? g.smem_learned : g.smem[dt];
-    const void *kern = dt == 1 ? reinterpret_cast<const void *>(mixed_i8_kernel<DMAX>)
-                       : learned ? reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, true>)
-                                 : reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, false>);
+    const bool team = dt == 0 && (g.wpf > 1 || g.fpb > 1);
+    const int smem1 = learned ? g.smem_learned : g.smem[dt];
+    // teams: each its one-warp region plus eight shared words, 16-byte aligned
+    const int team_bytes = (smem1 + 32 + 15) & ~15;
+    const int smem = team ? g.fpb * team_bytes : smem1;
+    const int threads = team ? 32 * g.wpf * g.fpb : 32;
+    if (team) {
+        int max_optin = 0;
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl.device);
+        if (smem > max_optin)
+            return fail(LDPC_ERR_UNSUPPORTED, "mixed decode: frames per block exceed shared memory");
+    }
+    const void *kern =
+        dt == 1   ? reinterpret_cast<const void *>(mixed_i8_kernel<DMAX>)
+        : team    ? (learned ? reinterpret_cast<const void *>(mixed_f32_team_kernel<DMAX, true>)
+                             : reinterpret_cast<const void *>(mixed_f32_team_kernel<DMAX, false>))
+        : learned ? reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, true>)
+                  : reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "mixed kernel attribute");
     int per_sm = 0, sms = 148;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "mixed occupancy");
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device);
     per_sm = std::max(per_sm, 1);
     if (g.per_sm[dt] > 0) per_sm = std::min(per_sm, g.per_sm[dt]);
-    const int grid = std::max(1, std::min(g.n_items[dt], per_sm * sms));
+    const int units = team ? (g.n_items[dt] + g.fpb - 1) / g.fpb : g.n_items[dt];
+    const int grid = std::max(1, std::min(units, per_sm * sms));
     unsigned long long *work = pl.d_work + 2 * gi + (dt == 1 ? 1 : 0);
     e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed work counter");
     const DevCode *codes = pl.set->d_desc;
-    if (dt == 0) {
+    if (team) {
+        const bool bulk = g.bulk_ok && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
+        if (learned)
+            mixed_f32_team_kernel<DMAX, true><<<grid, threads, smem, s>>>(
+                codes, g.d_items[0], g.n_items[0], pl.d_uframe, pl.d_llr_off, pl.d_hard_off,
+                static_cast<const float *>(d_in), p, d_hard, d_iters,
+                static_cast<float *>(d_post), work, bulk ? 1 : 0, pl.d_wptr, pl.d_wT, g.wpf, g.fpb,
+                team_bytes / 4);
+        else
+            mixed_f32_team_kernel<DMAX, false><<<grid, threads, smem, s>>>(
+                codes, g.d_items[0], g.n_items[0], pl.d_uframe, pl.d_llr_off, pl.d_hard_off,
+                static_cast<const float *>(d_in), p, d_hard, d_iters,
+                static_cast<float *>(d_post), work, bulk ? 1 : 0, nullptr, nullptr, g.wpf, g.fpb,
+                team_bytes / 4);
+    } else if (dt == 0) {
         const bool bulk = g.bulk_ok && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
         if (learned)
             mixed_f32_kernel<DMAX, true><<<grid, 32, smem, s>>>(
@@ -854,6 +956,39 @@ ldpc_status ldpc_mixed_group_info(const ldpc_mixed_plan *plan, int group, int *s
     return LDPC_OK;
 }
 
+ldpc_status ldpc_mixed_group_launch(ldpc_mixed_plan *plan, int group, ldpc_dtype dtype,
+                                    const ldpc_group_launch *set, ldpc_group_launch *get) {
+    if (!plan || group < 0 || group >= static_cast<int>(plan->p->groups.size()))
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_group_launch: bad plan or group");
+    if (dtype != LDPC_F32 && dtype != LDPC_I8X4)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_mixed_group_launch: unknown dtype");
+    MixedGroup &g = plan->p->groups[group];
+    const int dt = dtype == LDPC_F32 ? 0 : 1;
+    if (set) {
+        const bool f32 = dt == 0;
+        if (set->frames_per_item < 1 || set->frames_per_item > 1024 || set->blocks_per_sm < 0 ||
+            set->blocks_per_sm > 64 || set->warps_per_frame < 1 || set->frames_per_block < 1 ||
+            (f32 && (set->warps_per_frame > 3 || set->frames_per_block > 4)) ||
+            (!f32 && (set->warps_per_frame != 1 || set->frames_per_block != 1)))
+            return fail(LDPC_ERR_INVALID_ARG,
+                        "ldpc_mixed_group_launch: frames per item 1..1024, blocks per SM 0..64, "
+                        "FP32 warps per frame 1..3 and frames per block 1..4 (int8: 1 and 1)");
+        g.chunk[dt] = set->frames_per_item;
+        g.per_sm[dt] = set->blocks_per_sm;
+        if (f32) {
+            g.wpf = set->warps_per_frame;
+            g.fpb = set->frames_per_block;
+        }
+    }
+    if (get) {
+        get->frames_per_item = g.chunk[dt];
+        get->blocks_per_sm = g.per_sm[dt];
+        get->warps_per_frame = dt == 0 ? g.wpf : 1;
+        get->frames_per_block = dt == 0 ? g.fpb : 1;
+    }
+    return LDPC_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -1047,6 +1182,33 @@ static ldpc_status autotune_impl(MixedPlan &p, int lt, const void *d_in, const D
             if (st != LDPC_OK) break;
             if (ms < best) best = ms;
             else g.per_sm[dt] = old;
+        }
+    }
+    // FP32: warps per frame, then frames per block, per group (a setting the
+    // device cannot launch is skipped)
+    for (size_t gi = 0; st == LDPC_OK && dt == 0 && gi < p.groups.size(); ++gi) {
+        MixedGroup &g = p.groups[gi];
+        for (int knob = 0; knob < 2 && st == LDPC_OK; ++knob) {
+            for (int v : {1, 2, 3, 4}) {
+                if ((knob == 0 && (v > 3 || v == g.wpf)) || (knob == 1 && (v == 3 || v == g.fpb)))
+                    continue;
+                int &ref = knob == 0 ? g.wpf : g.fpb;
+                const int old = ref;
+                ref = v;
+                float ms = 0;
+                ldpc_status s2 = measure(&ms);
+                if (s2 == LDPC_ERR_UNSUPPORTED) {
+                    ref = old;
+                    continue;
+                }
+                if (s2 != LDPC_OK) {
+                    ref = old;
+                    st = s2;
+                    break;
+                }
+                if (ms < best) best = ms;
+                else ref = old;
+            }
         }
     }
     // concurrent groups (forked streams) or one after another

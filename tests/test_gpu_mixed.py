@@ -244,3 +244,40 @@ def test_mixed_learned_past_table_with_checkpoints(ldpc):
     h2, i2, p2 = plan.decode_learned(batch.llr, want_post=True, max_iters=16, stop_iter=si,
                                      stop_frac=sf)
     assert torch.equal(h2, hard) and torch.equal(i2, iters) and torch.equal(p2, post)
+
+
+@pytest.mark.parametrize("wpf,fpb", [(2, 1), (3, 1), (1, 2), (3, 4), (2, 4)])
+def test_mixed_f32_teams_bit_exact(ldpc, wpf, fpb):
+    """Warps per frame and frames per block (the FP32 launch settings the
+    autotuner searches) change the schedule only: plain FP32 and the learned
+    decoder with checkpoints give the same outputs as one warp per frame."""
+    shapes = _shapes()
+    codes, cs, plan, batch = _setup(ldpc, shapes, 700, seed=31, ebn0=(1.0, 3.5))
+    rng = np.random.default_rng(5)
+    ws = [rng.uniform(0.55, 1.0, (6, c.nnz_blocks)).astype(np.float32) for c in codes]
+    plan.set_weights([torch.from_numpy(w).cuda() for w in ws])
+    kw = dict(max_iters=16, stop_iter=(4, 9), stop_frac=(0.1, 0.04))
+    ref_f = plan.decode(batch.llr, ldpc.F32, max_iters=20, want_post=True)
+    ref_l = plan.decode_learned(batch.llr, want_post=True, **kw)
+    for gi in range(plan.n_groups):
+        got = plan.group_launch(gi, ldpc.F32, warps_per_frame=wpf, frames_per_block=fpb,
+                                frames_per_item=3)
+        assert got["warps_per_frame"] == wpf and got["frames_per_block"] == fpb
+    got_f = plan.decode(batch.llr, ldpc.F32, max_iters=20, want_post=True)
+    got_l = plan.decode_learned(batch.llr, want_post=True, **kw)
+    for a, b in zip(ref_f, got_f):
+        assert torch.equal(a, b)
+    for a, b in zip(ref_l, got_l):
+        assert torch.equal(a, b)
+
+
+def test_mixed_group_launch_argument_checks(ldpc):
+    shapes = _shapes()[:3]
+    codes = [ldpc.Code(s.hbm, s.z) for s in shapes]
+    plan = ldpc.MixedPlan(ldpc.CodeSet(codes), np.arange(12, dtype=np.int32) % 3)
+    with pytest.raises(ldpc.LdpcError):
+        plan.group_launch(0, ldpc.F32, warps_per_frame=4)
+    with pytest.raises(ldpc.LdpcError):
+        plan.group_launch(0, ldpc.I8X4, warps_per_frame=2)
+    with pytest.raises(ldpc.LdpcError):
+        plan.group_launch(0, ldpc.F32, frames_per_block=5)
