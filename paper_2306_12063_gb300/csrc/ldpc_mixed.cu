@@ -36,8 +36,10 @@ struct MixedItem {
 namespace {
 
 // One FP32 launch: work items of the group's codes, one frame at a time.
-// WT: learned normalised min-sum with code c's weights wptr[c] and
-// iteration count wT[c] (staged per iteration after the row state).
+// WT: learned normalised min-sum with code c's weights wptr[c], a table of
+// wT[c] rows (staged per iteration after the row state); each code runs
+// p.max_iters iterations when that is set, else wT[c], rows past the table
+// repeating its last one.
 template <int DMAX, bool WT = false>
 __global__ void __launch_bounds__(32)
     mixed_f32_kernel(const DevCode *__restrict__ codes, const MixedItem *__restrict__ items,
