@@ -602,6 +602,16 @@ ldpc_status ldpc_decode_layered_minsum_noalloc(const int16_t *hbm, int mb, int n
 ldpc_status ldpc_check_bounded_wait(const ldpc_code *code, uint32_t polls,
                                     cudaStream_t stream);
 
+/* Debug builds (-DLDPC_DEBUG) only: the number of clamps to [-127, 127]
+ * that the single-code int8 decoder took on real edges of decoded frames
+ * (eq. 22 and eq. 20 results, as the oracle counts them) since the last
+ * call; waits for `stream`, then reads and clears the count.  Release
+ * builds, which keep the decoder's instruction budget, return
+ * LDPC_ERR_UNSUPPORTED.  Saturation is the int8 decoder's specified
+ * arithmetic; the count tells how often it acted. */
+ldpc_status ldpc_debug_saturation_count(const ldpc_code *code, cudaStream_t stream,
+                                        int64_t *count);
+
 /* Testing aid (no counterpart in the paper): caps the number of blocks in
  * the persistent grids of the single-code FP32, int8 and learned decode
  * kernels for every later launch in the process; 0 (the default) removes

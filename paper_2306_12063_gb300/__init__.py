@@ -144,6 +144,7 @@ def load(build_if_missing: bool = False):
         "ldpc_mixed_paired_errors": ([vp, vp, vp, vp, vp, vp], i32),
         "ldpc_check_bounded_wait": ([vp, ctypes.c_uint32, vp], i32),
         "ldpc_test_set_grid_cap": ([i32], i32),
+        "ldpc_debug_saturation_count": ([vp, vp, P(i64)], i32),
         "ldpc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -413,6 +414,13 @@ class Code:
                                        ctypes.byref(p), _ptr(h_hard), _ptr(h_iters),
                                        _ptr(workspace), int(workspace.numel()),
                                        int(chunk_frames), _stream(stream)))
+
+    def saturation_count(self, stream=None) -> int:
+        """Debug builds: int8 clamps taken since the last call (waits for the
+        stream); raises LdpcError in release builds."""
+        v = ctypes.c_int64(0)
+        _check(load().ldpc_debug_saturation_count(self._h, _stream(stream), ctypes.byref(v)))
+        return int(v.value)
 
     def check_bounded_wait(self, polls: int = 4096, stream=None):
         """Runs the failure-path check; the next sync() raises the timeout."""

@@ -247,7 +247,7 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     if (e == cudaSuccess) e = cudaMalloc(&c.d_wgather, sizeof(int16_t) * wgather.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_colent, sizeof(uint32_t) * colent.size());
     if (e == cudaSuccess) e = cudaMalloc(&c.d_coloff, sizeof(int) * coloff.size());
-    if (e == cudaSuccess) e = cudaMalloc(&c.d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_status, 16);   // status word, saturation count
     if (e == cudaSuccess) e = cudaMalloc(&c.d_work, sizeof(unsigned long long) * kWorkSlots);
     if (e == cudaSuccess)
         e = cudaMemcpy(c.d_hbm, hbm, sizeof(int16_t) * mb * nb, cudaMemcpyHostToDevice);
@@ -269,7 +269,7 @@ ldpc_status ldpc_code_create(const int16_t *hbm, int mb, int nb, int z, ldpc_cod
     if (e == cudaSuccess)
         e = cudaMemcpy(c.d_coloff, coloff.data(), sizeof(int) * coloff.size(),
                        cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(c.d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c.d_status, 0, 16);
     if (e != cudaSuccess) {
         ldpc_status st = (e == cudaErrorMemoryAllocation)
                              ? fail(LDPC_ERR_NOMEM, "ldpc_code_create: device allocation")
@@ -538,6 +538,28 @@ ldpc_status ldpc_check_bounded_wait(const ldpc_code *code, uint32_t polls,
     ldpc_status st = bind(&code->c);
     if (st) return st;
     return launch_wait_check(code->c, polls, stream);
+}
+
+ldpc_status ldpc_debug_saturation_count(const ldpc_code *code, cudaStream_t stream,
+                                        int64_t *count) {
+    if (!code || !count)
+        return fail(LDPC_ERR_INVALID_ARG, "ldpc_debug_saturation_count: NULL argument");
+#ifdef LDPC_DEBUG
+    ldpc_status st = bind(&code->c);
+    if (st) return st;
+    LDPC_CUDA_TRY(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    unsigned long long v = 0;
+    LDPC_CUDA_TRY(cudaMemcpy(&v, code->c.d_status + 2, sizeof(v), cudaMemcpyDeviceToHost),
+                  "cudaMemcpy saturation count");
+    LDPC_CUDA_TRY(cudaMemset(code->c.d_status + 2, 0, sizeof(v)), "cudaMemset saturation count");
+    *count = static_cast<int64_t>(v);
+    return LDPC_OK;
+#else
+    (void)stream;
+    *count = 0;
+    return fail(LDPC_ERR_UNSUPPORTED,
+                "ldpc_debug_saturation_count: the library was built without -DLDPC_DEBUG");
+#endif
 }
 
 ldpc_status ldpc_sync(const ldpc_code *code, cudaStream_t stream, double timeout_s) {

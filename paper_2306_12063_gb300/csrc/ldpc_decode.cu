@@ -137,8 +137,12 @@ __global__ void __launch_bounds__(32)
         bool any = false;
         for (int b = 0; b < 4; ++b) any |= fr[b] >= 0;
         if (!any) break;
+        uint32_t live = 0;   // byte lanes decoding a frame (debug saturation count)
+#ifdef LDPC_DEBUG
+        for (int b = 0; b < 4; ++b) live |= fr[b] >= 0 ? 0xFFu << (8 * b) : 0u;
+#endif
         for (int l = 0; l < c.mb; ++l) {
-            layer_i8_any<DMAX, DM>(c, l, Zs, rows, lane, norm);
+            layer_i8_any<DMAX, DM>(c, l, Zs, rows, lane, norm, live);
             __syncwarp();
         }
         const uint32_t bad = p.early_stop ? syndrome_bad_i8<DMAX, DM>(c, Zs, lane) : 0x80808080u;

@@ -343,9 +343,36 @@ __device__ __forceinline__ void layer_f32_any(const DevCode &c, int layer, uint3
 // their Z_mn clamps to +127: never below a minimum.  Their stores change the
 // lane's dummy word, which the lane sets back to +127 after the row.
 // ---------------------------------------------------------------------------
+// Debug builds count the clamps the saturating additions take (eq. 22 and
+// eq. 20 results outside [-127, 127]) on the real edges of the byte lanes
+// set in `live` (0xFF per lane decoding a frame) into c.sat, the count the
+// oracle reports; release builds ignore `live`.
+#ifdef LDPC_DEBUG
+__device__ __forceinline__ uint32_t clamps_taken(uint32_t off_bytes_lo, uint32_t off_bytes_hi,
+                                                 uint32_t add, uint32_t live) {
+    // off_bytes_*: per frame b the offset-form value (0..254), frames 0, 2 in
+    // the 16-bit lanes of _lo and 1, 3 of _hi; add: two's-complement bytes
+    uint32_t n = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        if (!((live >> (8 * b)) & 0xFFu)) continue;
+        const uint32_t w = (b & 1) ? off_bytes_hi : off_bytes_lo;
+        const int v = static_cast<int>((w >> (16 * (b >> 1))) & 0xFFFFu);
+        const int a = static_cast<int>(static_cast<int8_t>((add >> (8 * b)) & 0xFFu));
+        n += (v + a < 0 || v + a > 254) ? 1u : 0u;
+    }
+    return n;
+}
+#endif
+
 template <int DS, int DMAX>
 __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uint32_t *Zs,
-                                         uint32_t *rows, int lane, bool norm) {
+                                         uint32_t *rows, int lane, bool norm,
+                                         uint32_t live = 0u) {
+    (void)live;
+#ifdef LDPC_DEBUG
+    uint32_t nsat = 0;
+#endif
     constexpr int SGW = sign_words(DMAX);
     constexpr uint32_t kB = 0x7F7F7F7Fu;   // bias of the running minima
     const int start = DMAX - d;
@@ -382,6 +409,9 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
             // 0xFF where slot i is not the argmin: (IDX ^ i) + 127 has bit 7 set
             const uint32_t nq = msb_bytes_to_mask(imad(IDX ^ (0x01010101u * i), one, kB));
             const uint32_t g = bsel(bsel(G2, G1, nq), bsel(M2, M1, nq), sm);      // -L_old
+#ifdef LDPC_DEBUG
+            if (i >= start) nsat += clamps_taken(lanes_even(u), lanes_odd(u), g, live);
+#endif
             // eq. (22): (Z + 127) - L_old, clamped to Z_mn + 127 in 0..254
             const uint32_t qe = add_clamp_off16x2(lanes_even(u), lanes_even_sx(g));
             const uint32_t qo = add_clamp_off16x2(lanes_odd(u), lanes_odd_sx(g));
@@ -423,6 +453,9 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
             const uint32_t at_min = msb_bytes_to_mask(imad(A[i], m_one, mn1p));
             id = bsel(id, 0x01010101u * i, at_min);
             const uint32_t y = bsel(bsel(Yn1, Yn2, at_min), bsel(Yp1, Yp2, at_min), pos);
+#ifdef LDPC_DEBUG
+            if (i >= start) nsat += clamps_taken(QE[i], QO[i], y, live);
+#endif
             // eq. (20): (Z_mn + 127) + L_new, clamped to Z + 127 in 0..254
             const uint32_t ze = add_clamp_off16x2(QE[i], lanes_even_sx(y));
             const uint32_t zo = add_clamp_off16x2(QO[i], lanes_odd_sx(y));
@@ -439,6 +472,9 @@ __device__ __forceinline__ void layer_i8(const DevCode &c, int layer, int d, uin
 #pragma unroll
         for (int k = 0; k < SGW; ++k) rs[3 + k] = ~(zsg[k] ^ P) | pad[k];
     }
+#ifdef LDPC_DEBUG
+    if (nsat && c.sat) atomicAdd(c.sat, static_cast<unsigned long long>(nsat));
+#endif
 }
 
 // A refilled byte lane must start with every message zero: clearing its
@@ -501,12 +537,13 @@ __device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint
 // One int8 layer through the instance that fits it.
 template <int DS, int DM = DS>
 __device__ __forceinline__ void layer_i8_any(const DevCode &c, int layer, uint32_t *Zs,
-                                             uint32_t *rows, int lane, bool norm) {
+                                             uint32_t *rows, int lane, bool norm,
+                                             uint32_t live = 0u) {
     const int d = __ldg(c.rowinfo + layer) & 255;
     if (use_sub_i8<DS, DM>(d))
-        layer_i8<DS, small_slots<DS, DM>()>(c, layer, d, Zs, rows, lane, norm);
+        layer_i8<DS, small_slots<DS, DM>()>(c, layer, d, Zs, rows, lane, norm, live);
     else
-        layer_i8<DS, DM>(c, layer, d, Zs, rows, lane, norm);
+        layer_i8<DS, DM>(c, layer, d, Zs, rows, lane, norm, live);
 }
 
 // ---------------------------------------------------------------------------

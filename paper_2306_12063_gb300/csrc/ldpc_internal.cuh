@@ -61,7 +61,8 @@ struct Code {
     uint32_t *d_colent = nullptr;    // [n_edges] per block column, block rows increasing:
                                      //   (block row << 20) | (block edge << 9) | shift
     int *d_coloff = nullptr;         // [nb + 1] start of each block column in d_colent
-    int *d_status = nullptr;         // device status word
+    int *d_status = nullptr;         // device status word; 8 bytes on, the int8 decoder's
+                                     // saturation count (debug builds)
     cudaStream_t aux[2] = {nullptr, nullptr};   // host-decode pipeline
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     size_t voff_words = 0;           // uint16 entries in d_voff
@@ -88,6 +89,7 @@ struct DevCode {
     const uint32_t *colent;   // [n_edges] column entries (block row, block edge, shift)
     const int *coloff;        // [nb + 1]
     int *status;
+    unsigned long long *sat;  // debug builds: int8 clamps taken (NULL: not counted)
 };
 
 inline DevCode dev_view(const Code &c) {
@@ -97,6 +99,7 @@ inline DevCode dev_view(const Code &c) {
     d.n_edges = c.n_edges; d.hbm = c.d_hbm; d.voff = c.d_voff;
     d.rowinfo = c.d_rowinfo; d.edges = c.d_edges; d.wgather = c.d_wgather;
     d.colent = c.d_colent; d.coloff = c.d_coloff; d.status = c.d_status;
+    d.sat = c.d_status ? reinterpret_cast<unsigned long long *>(c.d_status + 2) : nullptr;
     return d;
 }
 

@@ -180,6 +180,7 @@ extern "C" ldpc_status ldpc_decode_layered_minsum_noalloc(
     dc.colent = nullptr;
     dc.coloff = nullptr;
     dc.status = reinterpret_cast<int *>(scratch + 8);
+    dc.sat = nullptr;   // the debug saturation count needs a code handle
     DecodeParams p;
     p.max_iters = params->max_iters;
     p.alpha = params->normalise ? params->alpha : 1.0f;

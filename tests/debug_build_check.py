@@ -59,4 +59,20 @@ for shape in (synth.wifi_n648_r12(), synth.wifi_n1944_r56(), synth.tiny_z3_code(
                                      early_stop=True, want_post=True)
     code.sync()
     assert (gi.cpu().numpy() == wi).all() and (gp.cpu().numpy() == wp).all()
+# the int8 saturation count against the oracle's, on inputs heavy in +-127
+rng = np.random.default_rng(9)
+for shape in (synth.wifi_n648_r12(), synth.wifi_n1944_r56()):
+    rc = oracle.RefCode(shape.hbm, shape.z)
+    code = ldpc.Code(shape.hbm, shape.z)
+    F = 37
+    q = rng.choice(np.array([-127, -126, -3, -1, 0, 1, 2, 125, 127], dtype=np.int8),
+                   size=(F, rc.n))
+    code.saturation_count()   # clear
+    wh, wi, wp, events = rc.decode_layered_i8(q, 9, True, True)
+    gh, gi, gp = code.decode(torch.from_numpy(pack_i8(q)).cuda(), frames=F, dtype=ldpc.I8X4,
+                             max_iters=9, early_stop=True, want_post=True)
+    code.sync()
+    assert (gi.cpu().numpy() == wi).all() and (gp.cpu().numpy() == wp).all()
+    got = code.saturation_count()
+    assert events > 0 and got == events, (got, events)
 print("debug build ok")

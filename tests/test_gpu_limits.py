@@ -133,3 +133,12 @@ def test_bounded_wait_runs_out_and_is_reported(ldpc):
     code.sync()
     assert (gi.cpu().numpy() == wi).all()
     assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+
+
+def test_saturation_count_needs_the_debug_build(ldpc):
+    """The release build keeps the int8 decoder free of counting work."""
+    shape = synth.wifi_n648_r12()
+    code = ldpc.Code(shape.hbm, shape.z)
+    with pytest.raises(ldpc.LdpcError) as ei:
+        code.saturation_count()
+    assert ei.value.status == 6
