@@ -509,19 +509,30 @@ def learned_scale_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
     counts = np.bincount(cof, minlength=len(shapes))
     # per-code training on the library's own generators (bounded budget)
     t0 = time.time()
-    w_range, w_recipe, ranges = [], [], []
-    for ci, code in enumerate(codes):
+    # the codes train independently (and deterministically), four at a time
+    # on their own streams: one code's small batches leave the GPU mostly idle
+    from concurrent.futures import ThreadPoolExecutor
+    streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+
+    def train_code(ci):
         if counts[ci] == 0:
-            w_range.append(None)
-            w_recipe.append(None)
-            ranges.append(None)
-            continue
-        T = train.default_iterations(code.k / code.n)
-        rng_c = train.operating_range(code, LEARNED_EBN0[0], LEARNED_EBN0[1])
-        ranges.append(rng_c)
-        base = dict(T=T, steps=args.scale_train_steps, batch=1024, lr=2e-3, seed=1000 + ci)
-        w_range.append(train.train_weights(code, train.TrainConfig(ebn0_db=rng_c, **base)).weights)
-        w_recipe.append(train.train_weights(code, train.TrainConfig(**base)).weights)
+            return None, None, None
+        code = codes[ci]
+        s = streams[ci % len(streams)]
+        with torch.cuda.stream(s):
+            T = train.default_iterations(code.k / code.n)
+            rng_c = train.operating_range(code, LEARNED_EBN0[0], LEARNED_EBN0[1], stream=s)
+            base = dict(T=T, steps=args.scale_train_steps, batch=1024, lr=2e-3, seed=1000 + ci)
+            wr = train.train_weights(code, train.TrainConfig(ebn0_db=rng_c, **base), stream=s)
+            wc = train.train_weights(code, train.TrainConfig(**base), stream=s)
+            s.synchronize()
+            return rng_c, wr.weights, wc.weights
+
+    with ThreadPoolExecutor(len(streams)) as ex:
+        trained = list(ex.map(train_code, range(len(codes))))
+    ranges = [t[0] for t in trained]
+    w_range = [t[1] for t in trained]
+    w_recipe = [t[2] for t in trained]
     w_const = [None if w is None else torch.full_like(w, 0.75) for w in w_range]
     torch.cuda.synchronize()
     train_s = time.time() - t0

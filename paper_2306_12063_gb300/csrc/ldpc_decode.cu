@@ -193,7 +193,7 @@ static ldpc_status launch_decode_t(const Code &c, bool i8, const void *d_llr, in
     const int use_bulk = aligned ? 1 : 0;
     const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel<DMAX, DM>)
                           : reinterpret_cast<const void *>(decode_f32_kernel<DMAX, false, DM>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
@@ -248,7 +248,7 @@ static ldpc_status launch_learned_t(const Code &c, const float *d_llr, int64_t f
         return fail(LDPC_ERR_UNSUPPORTED, "decode: code too large for shared memory");
     const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (c.n % 4) == 0;
     const void *kern = reinterpret_cast<const void *>(decode_f32_kernel<DMAX, true>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
@@ -297,7 +297,7 @@ static ldpc_status launch_decode_view_t(const DevCode &dc, bool i8, const void *
     const bool aligned = (reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0 && (dc.n % 4) == 0;
     const void *kern = i8 ? reinterpret_cast<const void *>(decode_i8_kernel<DMAX>)
                           : reinterpret_cast<const void *>(decode_f32_kernel<DMAX>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return cuda_fail(e, "decode kernel attribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);

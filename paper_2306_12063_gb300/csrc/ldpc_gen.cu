@@ -354,8 +354,7 @@ ldpc_status launch_encode(const Code &c, const uint8_t *d_info, uint8_t *d_code,
                           int64_t frames, cudaStream_t s) {
     const int warp_bytes = (c.k + c.mb * c.z + c.z + 15) & ~15;
     const int smem = kEncWarps * warp_bytes;
-    cudaError_t e = cudaFuncSetAttribute(encode_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(encode_kernel));
     if (e != cudaSuccess) return cuda_fail(e, "encode_kernel attribute");
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);

@@ -103,6 +103,20 @@ inline DevCode dev_view(const Code &c) {
     return d;
 }
 
+// Lets `kern` take up to the current device's opt-in maximum of dynamic
+// shared memory; every launcher calls it before launching with its own size.
+// The attribute belongs to the kernel, not to a launch, so setting it to one
+// launch's size would race with another host thread launching the same
+// kernel for a larger code.
+inline cudaError_t allow_dynamic_smem(const void *kern) {
+    int dev = 0, mx = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
 // Thread-local last-error message, set by fail().
 void set_error(const std::string &msg);
 ldpc_status fail(ldpc_status st, const std::string &msg);

@@ -579,7 +579,7 @@ static ldpc_status launch_group_t(MixedPlan &pl, MixedGroup &g, int gi, int dt, 
                              : reinterpret_cast<const void *>(mixed_f32_team_kernel<DMAX, false>))
         : learned ? reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, true>)
                   : reinterpret_cast<const void *>(mixed_f32_kernel<DMAX, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return cuda_fail(e, "mixed kernel attribute");
     int per_sm = 0, sms = 148;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);

@@ -391,9 +391,7 @@ ldpc_status launch_forward_t(const Code &c, const float *llr, const uint8_t *bit
     const int wpb = warps_for(warp_bytes, c.device);
     if (wpb == 0) return fail(LDPC_ERR_UNSUPPORTED, "ldpc_learned_train_forward: code too large");
     const size_t smem = warp_bytes * wpb;
-    cudaError_t e = cudaFuncSetAttribute(train_forward_kernel<DMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(train_forward_kernel<DMAX>));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     const int64_t blocks = (frames + wpb - 1) / wpb;
     train_forward_kernel<DMAX><<<static_cast<unsigned>(blocks), 32 * wpb, smem, s>>>(
@@ -412,9 +410,7 @@ ldpc_status launch_backward_t(const Code &c, const float *llr, const uint8_t *bi
     const int wpb = warps_for(sizeof(float) * wf, c.device);
     if (wpb == 0) return fail(LDPC_ERR_UNSUPPORTED, "ldpc_learned_train_backward: code too large");
     const size_t smem = sizeof(float) * wf * wpb;
-    cudaError_t e = cudaFuncSetAttribute(train_backward_kernel<DMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(train_backward_kernel<DMAX>));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     const int64_t blocks = (frames + wpb - 1) / wpb;
     train_backward_kernel<DMAX><<<static_cast<unsigned>(blocks), 32 * wpb, smem, s>>>(

@@ -361,7 +361,7 @@ ldpc_status launch_i16w_t(const Code &c, const int16_t *llr, int64_t frames,
     if (smem > smem_optin(c.device))
         return fail(LDPC_ERR_UNSUPPORTED, "decode (int16): code too large for shared memory");
     const void *kern = reinterpret_cast<const void *>(decode_i16w_kernel<DMAX>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return cuda_fail(e, "decode (int16) attribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
@@ -386,8 +386,7 @@ ldpc_status launch_flooding_t(const Code &c, const float *llr, int64_t frames,
     if (smem > static_cast<size_t>(smem_optin(c.device)))
         return fail(LDPC_ERR_UNSUPPORTED, "flooding decode: code too large for shared memory");
     const void *kern = reinterpret_cast<const void *>(decode_flooding_kernel<DMAX>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return cuda_fail(e, "flooding attribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
@@ -451,8 +450,7 @@ ldpc_status ldpc_encode_bitmap(const ldpc_code *code, const uint32_t *d_info, ui
     const int zw = c.z / 32;
     const int warp_words = (c.kb + c.mb + 2) * zw;
     const int smem = kBitmapWarps * warp_words * 4;
-    e = cudaFuncSetAttribute(encode_bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
+    e = allow_dynamic_smem(reinterpret_cast<const void *>(encode_bitmap_kernel));
     if (e != cudaSuccess) return cuda_fail(e, "encode_bitmap attribute");
     const int64_t blocks =
         std::min<int64_t>((frames + kBitmapWarps - 1) / kBitmapWarps, 32LL * sm_count(c.device));
