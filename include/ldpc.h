@@ -613,10 +613,11 @@ ldpc_status ldpc_debug_saturation_count(const ldpc_code *code, cudaStream_t stre
                                         int64_t *count);
 
 /* Testing aid (no counterpart in the paper): caps the number of blocks in
- * the persistent grids of the single-code FP32, int8 and learned decode
- * kernels for every later launch in the process; 0 (the default) removes
- * the cap.  Under a small cap each block decodes many frames, which drives
- * the dynamic frame hand-out (per byte lane for int8) on small batches.
+ * the persistent grids of the single-code FP32, int8, int16 and learned
+ * decode kernels for every later launch in the process; 0 (the default)
+ * removes the cap.  Under a small cap each block decodes many frames, which
+ * drives the dynamic frame hand-out (per byte or 16-bit lane for the packed
+ * decoders) on small batches.
  * A negative cap returns LDPC_ERR_INVALID_ARG. */
 ldpc_status ldpc_test_set_grid_cap(int blocks);
 

@@ -34,7 +34,9 @@ namespace ldpc {
 // ldpc_test_set_grid_cap.
 static std::atomic<int> g_grid_cap{0};
 
-static int64_t grid_cap(int64_t cap) {
+// `cap` lowered to the testing cap, if one is set.
+
+int64_t grid_cap(int64_t cap) {
     const int v = g_grid_cap.load(std::memory_order_relaxed);
     return v > 0 ? std::min<int64_t>(cap, v) : cap;
 }

@@ -162,6 +162,8 @@ ldpc_status launch_paired(const Code &c, const uint8_t *d_info, const uint32_t *
                           const uint32_t *d_hard_b, int64_t frames, int64_t *d_counts,
                           cudaStream_t s);
 ldpc_status launch_wait_check(const Code &c, uint32_t polls, cudaStream_t s);
+// A persistent grid size lowered to the cap set by ldpc_test_set_grid_cap.
+int64_t grid_cap(int64_t cap);
 // Zeroes the next work-counter slot on stream s and returns it (NULL and an
 // error message on failure).
 unsigned long long *work_slot(const Code &c, cudaStream_t s);

@@ -148,6 +148,225 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same decoder with two frames per 32-bit word, one per 16-bit lane
+// (frame 2g in bits 0-15, 2g + 1 in bits 16-31): the wrap-around additions
+// are single packed add-max instructions (a + b per lane modulo 2^16, then
+// the max with -32768, which keeps it), and |x|, the minima and the masks
+// act on both frames at once.  Row state per check row, five words:
+// [N1, N2, IDX] with a frame per lane (scaled minima, argmin slot) and
+// [SGA, SGB], the message signs of each frame at bit DMAX - 1 - i for slot
+// i.  The results are those of layer_i16w, lane by lane.
+// ---------------------------------------------------------------------------
+constexpr int kRowWordsI16x2 = 5;
+
+// a + b per 16-bit lane, modulo 2^16
+__device__ __forceinline__ uint32_t wadd16x2(uint32_t a, uint32_t b) {
+    return __viaddmax_s16x2(a, b, 0x80008000u);
+}
+// -a per 16-bit lane, modulo 2^16 (-(-32768) stays -32768)
+__device__ __forceinline__ uint32_t wneg16x2(uint32_t a) { return wadd16x2(~a, 0x00010001u); }
+__device__ __forceinline__ uint32_t smin16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t smax16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t umin16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// 0xFFFF in each lane whose bit 15 is set (prmt sign replication)
+__device__ __forceinline__ uint32_t lane_sign_mask(uint32_t x) { return prmt(x, 0u, 0xBB99u); }
+// 0xFFFF in each lane where a == b
+__device__ __forceinline__ uint32_t lane_eq_mask(uint32_t a, uint32_t b, uint32_t one) {
+    const uint32_t t = umin16x2(a ^ b, 0x00010001u) ^ 0x00010001u;   // 1 where equal
+    return imad(t, 0xFFFFu * one, 0u);
+}
+// floor(3 m / 4) per lane, wrapped (the (3m) >> 2 of layer_i16w)
+__device__ __forceinline__ uint32_t scale34_16x2(uint32_t m) {
+    const int lo = static_cast<int16_t>(m & 0xFFFFu), hi = static_cast<int16_t>(m >> 16);
+    return (static_cast<uint32_t>(wrap16((3 * lo) >> 2)) & 0xFFFFu) |
+           (static_cast<uint32_t>(wrap16((3 * hi) >> 2)) << 16);
+}
+
+template <int DMAX>
+__device__ __forceinline__ void layer_i16x2(const DevCode &c, int layer, uint32_t *Zs,
+                                            uint32_t *rows, int lane, bool norm) {
+    const uint32_t ri = __ldg(c.rowinfo + layer);
+    const int d = ri & 255;
+    const int start = DMAX - d;
+    const uint32_t one = opaque_one(c.z);
+    for (int t = 0; t < c.rpl; ++t) {
+        const int r = lane + 32 * t;
+        if (r >= c.z) break;
+        uint32_t *rs = rows + (layer * c.z + r) * kRowWordsI16x2;
+        const uint32_t N1 = rs[0], N2 = rs[1], IDX = rs[2], SGA = rs[3], SGB = rs[4];
+        const uint32_t G1 = wneg16x2(N1), G2 = wneg16x2(N2);   // -N per lane
+        const uint16_t *vrow = c.voff + (layer * c.rpl + t) * (DMAX * 32) + lane;
+        uint32_t off[DMAX], Q[DMAX], A[DMAX];
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) off[i] = edge_off(c, vrow + i * 32);
+        uint32_t mn1 = 0x7FFF7FFFu, mn2 = 0x7FFF7FFFu, sx = 0;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t z = lds_u32(Zs, off[i]);
+            // 0xFFFF where slot i is not the lane's argmin: (IDX ^ i) + 0x7FFF
+            // has bit 15 set (no carry between lanes: IDX <= 26)
+            const uint32_t nq = lane_sign_mask(imad(IDX ^ (0x00010001u * i), one, 0x7FFF7FFFu));
+            // 0xFFFF where the old message of slot i is negative
+            const int b = DMAX - 1 - i;
+            const uint32_t sm = prmt(SGA << (31 - b), SGB << (31 - b), 0xFFBBu);
+            // -L_old per lane: M for a negative message, -M for a positive one;
+            // 0 for the leading unused slots
+            uint32_t g = bsel(bsel(G2, G1, nq), bsel(N2, N1, nq), sm);
+            g = i < start ? 0u : g;
+            const uint32_t q = wadd16x2(z, g);                 // eq. (22)
+            const uint32_t a = smax16x2(q, wneg16x2(q));       // |Z_mn| in 16 bits
+            Q[i] = q;
+            A[i] = a;
+            mn2 = smax16x2(mn1, smin16x2(mn2, a));
+            mn1 = smin16x2(mn1, a);
+            sx ^= q;
+        }
+        const uint32_t n1 = norm ? scale34_16x2(mn1) : mn1;   // eq. (23) magnitudes
+        const uint32_t n2 = norm ? scale34_16x2(mn2) : mn2;
+        const uint32_t h1 = wneg16x2(n1), h2 = wneg16x2(n2);
+        uint32_t nsa = 0, nsb = 0, id = 0;
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            const uint32_t at_min = lane_eq_mask(A[i], mn1, one);
+            id = bsel(id, 0x00010001u * i, at_min);
+            const uint32_t sg = lane_sign_mask(sx ^ Q[i]);   // message sign per lane
+            const uint32_t L = bsel(bsel(n1, n2, at_min), bsel(h1, h2, at_min), sg);
+            if (i >= start) sts_u32(Zs, off[i], wadd16x2(Q[i], L));   // eq. (20)
+            nsa = __funnelshift_l(sg << 16, nsa, 1);
+            nsb = __funnelshift_l(sg, nsb, 1);
+        }
+        rs[0] = n1;
+        rs[1] = n2;
+        rs[2] = id;
+        rs[3] = nsa;
+        rs[4] = nsb;
+    }
+}
+
+// Bit 15 (frame of lane 0) and bit 31 (lane 1) set where a check fails.
+template <int DMAX>
+__device__ __forceinline__ uint32_t syndrome_bad_i16x2(const DevCode &c, const uint32_t *Zs,
+                                                       int lane) {
+    uint32_t bad = 0;
+    for (int l = 0; l < c.mb; ++l) {
+        for (int t = 0; t < c.rpl; ++t) {
+            if (lane + 32 * t >= c.z) break;
+            const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
+            uint32_t par = 0;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) {
+                const uint32_t v = lds_u32(Zs, edge_off(c, vrow + i * 32));
+                par ^= v | wadd16x2(v, 0xFFFFFFFFu);   // bit 15 / 31 set iff Z <= 0
+            }
+            bad |= par;
+        }
+    }
+    return __reduce_or_sync(0xFFFFFFFFu, bad & 0x80008000u);
+}
+
+// Lane `half` (0 or 1) of the packed posteriors, sign-extended.
+__device__ __forceinline__ int lane16(uint32_t w, int half) {
+    return static_cast<int16_t>((w >> (16 * half)) & 0xFFFFu);
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(32)
+    decode_i16x2_kernel(DevCode c, const int16_t *__restrict__ llr, int64_t frames,
+                        DecodeParams p, uint32_t *__restrict__ hard, int32_t *__restrict__ iters,
+                        int16_t *__restrict__ post, unsigned long long *work) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    uint32_t *Zs = smem;
+    uint32_t *rows = Zs + posterior_words(c.n);
+    const bool norm = p.normalise != 0;
+    const int64_t g0 = blockIdx.x;
+    if (2 * g0 >= frames) return;
+    int64_t fr[2];
+    int kb[2];
+    for (int b = 0; b < 2; ++b) {
+        fr[b] = 2 * g0 + b < frames ? 2 * g0 + b : -1;
+        kb[b] = 0;
+    }
+    // a lane without a frame holds +1023 (the all-zero codeword, which stops
+    // after one iteration)
+    for (int i = lane; i < c.n; i += 32) {
+        const uint32_t lo = fr[0] >= 0 ? static_cast<uint16_t>(llr[fr[0] * c.n + i]) : 1023u;
+        const uint32_t hi = fr[1] >= 0 ? static_cast<uint16_t>(llr[fr[1] * c.n + i]) : 1023u;
+        Zs[i] = lo | (hi << 16);
+    }
+    for (int i = lane; i < c.m * kRowWordsI16x2; i += 32) rows[i] = 0u;
+    Zs[c.n + lane] = 0x7FFF7FFFu;   // dummy posterior +32767 in both lanes
+    __syncwarp();
+    const int64_t dyn_base = 2 * static_cast<int64_t>(gridDim.x);
+    int64_t pend = next_work(work, dyn_base, lane);
+    if (pend < frames) prefetch_l2(llr + pend * c.n, 2u * static_cast<uint32_t>(c.n), lane);
+    for (;;) {
+        if (fr[0] < 0 && fr[1] < 0) break;
+        for (int l = 0; l < c.mb; ++l) {
+            layer_i16x2<DMAX>(c, l, Zs, rows, lane, norm);
+            __syncwarp();
+        }
+        const uint32_t bad = p.early_stop ? syndrome_bad_i16x2<DMAX>(c, Zs, lane) : 0x80008000u;
+        for (int b = 0; b < 2; ++b) {
+            if (fr[b] < 0) continue;
+            kb[b] += 1;
+            const bool ok = !((bad >> (16 * b + 15)) & 1u);
+            if (!ok && kb[b] < p.max_iters) continue;
+            // frame finished: outputs, then the next frame into this lane
+            uint32_t *h = hard + fr[b] * c.nwords;
+            for (int wb = 0; wb < c.nwords; wb += 32) {
+                uint32_t mine = 0;
+                for (int i = 0; i < 32 && wb + i < c.nwords; ++i) {
+                    const int n = (wb + i) * 32 + lane;
+                    const bool hb = n < c.n && lane16(Zs[n], b) <= 0;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hb);
+                    if (lane == i) mine = bal;
+                }
+                if (wb + lane < c.nwords) h[wb + lane] = mine;
+            }
+            if (lane == 0) iters[fr[b]] = kb[b];
+            if (post)
+                for (int n = lane; n < c.n; n += 32)
+                    post[fr[b] * c.n + n] = static_cast<int16_t>(lane16(Zs[n], b));
+            const int64_t nf = pend;
+            if (nf >= frames) {
+                fr[b] = -1;
+                continue;
+            }
+            pend = next_work(work, dyn_base, lane);
+            if (pend < frames) prefetch_l2(llr + pend * c.n, 2u * static_cast<uint32_t>(c.n), lane);
+            fr[b] = nf;
+            kb[b] = 0;
+            const uint32_t keep = b ? 0x0000FFFFu : 0xFFFF0000u;
+            __syncwarp();
+            for (int i = lane; i < c.n; i += 32) {
+                const uint32_t v = static_cast<uint16_t>(llr[nf * c.n + i]);
+                Zs[i] = (Zs[i] & keep) | (v << (16 * b));
+            }
+            // zero minima make every old message of the lane zero
+            for (int r = lane; r < c.m; r += 32) {
+                uint32_t *rs = rows + r * kRowWordsI16x2;
+                rs[0] &= keep;
+                rs[1] &= keep;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 __global__ void quantize_i16_kernel(const float *__restrict__ llr, int16_t *__restrict__ q,
                                     int64_t count, float scale, float lim) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
@@ -357,6 +576,25 @@ template <int DMAX>
 ldpc_status launch_i16w_t(const Code &c, const int16_t *llr, int64_t frames,
                           const DecodeParams &p, uint32_t *hard, int32_t *iters, int16_t *post,
                           cudaStream_t s) {
+    // two frames per word when the packed row state fits, else one per warp
+    const int smem2 = 4 * (posterior_words(c.n) + c.m * kRowWordsI16x2);
+    if (smem2 <= smem_optin(c.device)) {
+        const void *kern = reinterpret_cast<const void *>(decode_i16x2_kernel<DMAX>);
+        cudaError_t e = allow_dynamic_smem(kern);
+        if (e != cudaSuccess) return cuda_fail(e, "decode (int16) attribute");
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem2);
+        if (e != cudaSuccess) return cuda_fail(e, "decode (int16) occupancy");
+        const int64_t units = (frames + 1) / 2;
+        const int grid = static_cast<int>(std::min<int64_t>(
+            units, grid_cap(static_cast<int64_t>(std::max(per_sm, 1)) * sm_count(c.device))));
+        unsigned long long *work = work_slot(c, s);
+        if (!work) return LDPC_ERR_CUDA;
+        decode_i16x2_kernel<DMAX><<<grid, 32, smem2, s>>>(dev_view(c), llr, frames, p, hard,
+                                                          iters, post, work);
+        e = cudaGetLastError();
+        return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "decode (int16) launch");
+    }
     const int smem = 4 * (posterior_words(c.n) + c.m * 3);
     if (smem > smem_optin(c.device))
         return fail(LDPC_ERR_UNSUPPORTED, "decode (int16): code too large for shared memory");

@@ -66,6 +66,26 @@ def test_int16_wrap_decoder_bit_exact(ldpc, shape, ebn0, iters, norm, es):
     assert (gp.cpu().numpy() == wp).all()
 
 
+@pytest.mark.parametrize("shape,frames", [(synth.wifi_n648_r12(), 151),
+                                          (synth.wifi_n1944_r56(), 77)])
+def test_int16_lane_refills(ldpc, request, shape, frames):
+    """Two frames per word, each 16-bit lane refilled on its own as its frame
+    stops: one block decodes every frame, at low Eb/N0 so the iteration
+    counts vary widely."""
+    ldpc.set_grid_cap(1)
+    request.addfinalizer(lambda: ldpc.set_grid_cap(0))
+    rc, _, _, llr = _llr(shape, frames, 1.5 if shape.mb > 4 else 3.0)
+    q = oracle.quantize_i16(llr, 16.0, 10)
+    wh, wi, wp, _ = rc.decode_layered_i16w(q, 15, normalise=True, early_stop=True)
+    code = ldpc.Code(shape.hbm, shape.z)
+    gh, gi, gp = code.decode(torch.from_numpy(q).cuda(), dtype=ldpc.I16W, max_iters=15,
+                             normalise=True, early_stop=True, want_post=True)
+    assert (gi.cpu().numpy() == wi).all()
+    assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+    assert (gp.cpu().numpy() == wp).all()
+    assert len(set(wi.tolist())) > 5 and wi.max() == 15
+
+
 def test_int16_wrap_overflow_cases(ldpc):
     """Inputs far beyond Q_B (up to the int16 limits): many wraps, including
     |-32768|; the GPU follows the oracle through every one."""
