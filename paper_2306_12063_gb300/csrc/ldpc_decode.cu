@@ -147,7 +147,10 @@ __global__ void __launch_bounds__(32)
             layer_i8_any<DMAX, DM>(c, l, Zs, rows, lane, norm, live);
             __syncwarp();
         }
-        const uint32_t bad = p.early_stop ? syndrome_bad_i8<DMAX, DM>(c, Zs, lane) : 0x80808080u;
+        uint32_t need = 0;   // bit 7 of every byte lane decoding a frame
+        for (int b = 0; b < 4; ++b) need |= fr[b] >= 0 ? 0x80u << (8 * b) : 0u;
+        const uint32_t bad =
+            p.early_stop ? syndrome_bad_i8<DMAX, DM>(c, Zs, lane, need) : 0x80808080u;
         for (int b = 0; b < 4; ++b) {
             if (fr[b] < 0) continue;
             kb[b] += 1;

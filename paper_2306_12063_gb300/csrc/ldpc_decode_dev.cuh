@@ -289,16 +289,20 @@ __device__ __forceinline__ int syndrome_count_f32(const DevCode &c, const uint32
     return static_cast<int>(__reduce_add_sync(kFull, cnt));
 }
 
-// True when every check holds.
+// True when every check holds.  The scan ends at the first layer with an
+// unsatisfied check: a frame that has not converged usually fails in the
+// first layer it looks at, so only the iteration that ends a frame pays
+// for a full pass over the edges.
 template <int DS, int DM = DS>
 __device__ __forceinline__ bool syndrome_ok_f32(const DevCode &c, const uint32_t *Zs, int lane) {
-    uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
         const int d = __ldg(c.rowinfo + l) & 255;
-        bad |= use_sub<DS, DM>(d) ? syndrome_rows_f32<DS, small_slots<DS, DM>()>(c, Zs, l, lane)
-                                  : syndrome_rows_f32<DS, DM>(c, Zs, l, lane);
+        const uint32_t bad = use_sub<DS, DM>(d)
+                                 ? syndrome_rows_f32<DS, small_slots<DS, DM>()>(c, Zs, l, lane)
+                                 : syndrome_rows_f32<DS, DM>(c, Zs, l, lane);
+        if (__any_sync(kFull, bad >> 31)) return false;
     }
-    return !__any_sync(kFull, bad >> 31);
+    return true;
 }
 
 // One FP32 layer through the instance that fits it.  Learned weights are
@@ -520,16 +524,21 @@ __device__ __forceinline__ uint32_t syndrome_rows_i8(const DevCode &c, const uin
     return bad;
 }
 
-// int8 syndrome: bit 7 of byte b set when frame b has an unsatisfied check.
+// int8 syndrome: bit 7 of byte b set when frame b has an unsatisfied check,
+// for the byte lanes of `need` (bit 7 of each byte lane decoding a frame);
+// the other lanes' bits are unspecified.  The scan ends once every lane of
+// `need` has an unsatisfied check.
 template <int DS, int DM = DS>
 __device__ __forceinline__ uint32_t syndrome_bad_i8(const DevCode &c, const uint32_t *Zs,
-                                                    int lane) {
+                                                    int lane, uint32_t need = 0x80808080u) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
         const int d = __ldg(c.rowinfo + l) & 255;
         bad |= use_sub_i8<DS, DM>(d)
                    ? syndrome_rows_i8<DS, small_slots<DS, DM>()>(c, Zs, l, lane)
                    : syndrome_rows_i8<DS, DM>(c, Zs, l, lane);
+        const uint32_t all = __reduce_or_sync(kFull, bad & 0x80808080u);
+        if ((all & need) == need) return all;
     }
     return __reduce_or_sync(kFull, bad & 0x80808080u);
 }
@@ -688,9 +697,9 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
                                     wcur + l * WP);
             __syncwarp();
         }
-        if (checkpoints) {
-            // count the unsatisfied checks: none ends the frame (eq. 21), too
-            // many at a give-up checkpoint ends it too
+        if (checkpoints && (k == p.stop_iter[0] || k == p.stop_iter[1])) {
+            // a give-up checkpoint: count the unsatisfied checks; none ends
+            // the frame (eq. 21), too many ends it too
             const int u = syndrome_count_f32<DMAX, DM>(c, Zs, lane);
             if (u == 0 || (k == p.stop_iter[0] && u > lim0) || (k == p.stop_iter[1] && u > lim1))
                 return k;
@@ -716,8 +725,9 @@ __device__ __forceinline__ void team_sync(int id, int nw) {
         asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nw * 32) : "memory");
 }
 
-// This warp's part of the syndrome: bit 31 set (warp-uniform) when one of
-// its rows fails, or (count) the number of its failing rows.
+// This warp's part of the syndrome: 1 when one of its rows fails (the scan
+// ends at the first layer where one does), 0 otherwise; or (count) the
+// number of its failing rows.
 template <int DS, int DM>
 __device__ __forceinline__ uint32_t syndrome_part_f32(const DevCode &c, const uint32_t *Zs, int lane,
                                                       int t0, int tstep, bool count) {
@@ -731,8 +741,9 @@ __device__ __forceinline__ uint32_t syndrome_part_f32(const DevCode &c, const ui
                                      : syndrome_row_f32<DS, DM>(c, Zs, l, t, lane);
             acc = count ? acc + (par >> 31) : (acc | par);
         }
+        if (!count && __any_sync(kFull, acc >> 31)) return 1u;
     }
-    return count ? __reduce_add_sync(kFull, acc) : (__any_sync(kFull, acc >> 31) ? 1u : 0u);
+    return count ? __reduce_add_sync(kFull, acc) : 0u;
 }
 
 // decode_one_f32 for a team of tstep warps (wi: this warp's index in it).
@@ -790,13 +801,14 @@ __device__ __forceinline__ int decode_one_f32_team(const DevCode &c, uint32_t *Z
             team_sync(bar_id, tstep);
         }
         if (p.early_stop) {
-            const uint32_t part = syndrome_part_f32<DMAX, DMAX>(c, Zs, lane, wi, tstep, checkpoints);
+            const bool count = checkpoints && (k == p.stop_iter[0] || k == p.stop_iter[1]);
+            const uint32_t part = syndrome_part_f32<DMAX, DMAX>(c, Zs, lane, wi, tstep, count);
             if (lane == 0) tw[1 + wi] = static_cast<int>(part);
             team_sync(bar_id, tstep);
             int u = 0;
             for (int w = 0; w < tstep; ++w) u += tw[1 + w];
-            if (u == 0 || (checkpoints && ((k == p.stop_iter[0] && u > lim0) ||
-                                           (k == p.stop_iter[1] && u > lim1))))
+            if (u == 0 || (count && ((k == p.stop_iter[0] && u > lim0) ||
+                                     (k == p.stop_iter[1] && u > lim1))))
                 return k;
         }
     }

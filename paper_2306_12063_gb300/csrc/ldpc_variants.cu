@@ -82,10 +82,11 @@ __device__ __forceinline__ void layer_i16w(const DevCode &c, int layer, uint32_t
     }
 }
 
+// True when every check holds; the scan ends at the first failing layer.
 template <int DMAX>
 __device__ __forceinline__ bool syndrome_ok_int(const DevCode &c, const uint32_t *Zs, int lane) {
-    uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
+        uint32_t bad = 0;
         for (int t = 0; t < c.rpl; ++t) {
             if (lane + 32 * t >= c.z) break;
             const uint16_t *vrow = c.voff + (l * c.rpl + t) * (DMAX * 32) + lane;
@@ -95,8 +96,9 @@ __device__ __forceinline__ bool syndrome_ok_int(const DevCode &c, const uint32_t
                 par ^= static_cast<int>(lds_u32(Zs, edge_off(c, vrow + i * 32))) <= 0 ? 1u : 0u;
             bad |= par;
         }
+        if (__any_sync(0xFFFFFFFFu, bad)) return false;
     }
-    return !__any_sync(0xFFFFFFFFu, bad);
+    return true;
 }
 
 template <int DMAX>
@@ -256,10 +258,12 @@ __device__ __forceinline__ void layer_i16x2(const DevCode &c, int layer, uint32_
     }
 }
 
-// Bit 15 (frame of lane 0) and bit 31 (lane 1) set where a check fails.
+// Bit 15 (frame of lane 0) and bit 31 (lane 1) set where a check fails, for
+// the lanes of `need` (bit 15 / 31 of each lane decoding a frame; the others'
+// bits are unspecified); the scan ends once all of them have failed.
 template <int DMAX>
 __device__ __forceinline__ uint32_t syndrome_bad_i16x2(const DevCode &c, const uint32_t *Zs,
-                                                       int lane) {
+                                                       int lane, uint32_t need) {
     uint32_t bad = 0;
     for (int l = 0; l < c.mb; ++l) {
         for (int t = 0; t < c.rpl; ++t) {
@@ -273,6 +277,8 @@ __device__ __forceinline__ uint32_t syndrome_bad_i16x2(const DevCode &c, const u
             }
             bad |= par;
         }
+        const uint32_t all = __reduce_or_sync(0xFFFFFFFFu, bad & 0x80008000u);
+        if ((all & need) == need) return all;
     }
     return __reduce_or_sync(0xFFFFFFFFu, bad & 0x80008000u);
 }
@@ -319,7 +325,9 @@ __global__ void __launch_bounds__(32)
             layer_i16x2<DMAX>(c, l, Zs, rows, lane, norm);
             __syncwarp();
         }
-        const uint32_t bad = p.early_stop ? syndrome_bad_i16x2<DMAX>(c, Zs, lane) : 0x80008000u;
+        const uint32_t need = (fr[0] >= 0 ? 0x8000u : 0u) | (fr[1] >= 0 ? 0x80000000u : 0u);
+        const uint32_t bad =
+            p.early_stop ? syndrome_bad_i16x2<DMAX>(c, Zs, lane, need) : 0x80008000u;
         for (int b = 0; b < 2; ++b) {
             if (fr[b] < 0) continue;
             kb[b] += 1;
