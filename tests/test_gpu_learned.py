@@ -34,17 +34,15 @@ def _weights(rc, T, seed, lo=0.4, hi=1.0):
     return rng.uniform(lo, hi, size=(T, rc.nnz_blocks)).astype(np.float32)
 
 
-# T = 16 on the N=648 code is the largest whole table kept in shared memory
-# (16 x 12 layers x 8 slots x 4 bytes); T = 17 and 20 stage two rows per
-# iteration instead.
+# long tables (T = 16, 17, 20): every iteration stages a new row
 @pytest.mark.parametrize("shape,T,ebn0,frames", [(synth.wifi_n648_r12(), 8, 2.0, 333),
                                                  (synth.wifi_n1944_r56(), 6, 4.0, 257),
                                                  (synth.wimax_mixed_set()[-4], 8, 1.8, 41),
                                                  (synth.wifi_n648_r12(), 16, 1.5, 200),
                                                  (synth.wifi_n648_r12(), 17, 1.5, 200),
                                                  (synth.wifi_n1944_r56(), 20, 3.0, 120)],
-                         ids=["wifi648", "wifi1944", "wimax2304", "wifi648_T16_table",
-                              "wifi648_T17_rows", "wifi1944_T20_rows"])
+                         ids=["wifi648", "wifi1944", "wimax2304", "wifi648_T16",
+                              "wifi648_T17", "wifi1944_T20"])
 def test_learned_bit_exact(ldpc, shape, T, ebn0, frames):
     rc, _, llr = _inputs(shape, frames, ebn0)
     w = _weights(rc, T, 5)

@@ -213,9 +213,8 @@ def test_mixed_learned_and_fallback(ldpc):
 def test_mixed_learned_past_table_with_checkpoints(ldpc):
     """The mixed learned launches with every code run up to 16 iterations
     (rows past T_c repeating the last) and two give-up checkpoints equal the
-    oracle's decoder frame by frame.  Every third code has a 40-row table,
-    too large to keep whole in shared memory (two rows are staged per
-    iteration), next to codes whose whole table is staged."""
+    oracle's decoder frame by frame.  Every third code has a 40-row table
+    (a new row staged at every iteration), the others 3 to 8 rows."""
     shapes = _shapes()
     codes, cs, plan, batch = _setup(ldpc, shapes, 500, seed=21, ebn0=(1.0, 3.5))
     rng = np.random.default_rng(8)
@@ -256,7 +255,7 @@ def test_mixed_f32_teams_bit_exact(ldpc, wpf, fpb):
     shapes = _shapes()
     codes, cs, plan, batch = _setup(ldpc, shapes, 700, seed=31, ebn0=(1.0, 3.5))
     rng = np.random.default_rng(5)
-    # 6-row tables are staged whole, 40-row ones two rows per iteration
+    # 6-row and 40-row tables (the latter past every iteration run here)
     ws = [rng.uniform(0.55, 1.0, (40 if ci % 2 else 6, c.nnz_blocks)).astype(np.float32)
           for ci, c in enumerate(codes)]
     plan.set_weights([torch.from_numpy(w).cuda() for w in ws])
