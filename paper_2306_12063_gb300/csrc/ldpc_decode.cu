@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(32)
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *Zs = smem + 4;
     uint32_t *rows = Zs + posterior_words(c.n);   // Z_n words, then the per-lane dummy words
-    // learned weights of two iterations, [2][mb][wpad(DMAX)], 16-byte aligned
+    // learned weights, [kWeightBuffers][mb][wpad(DMAX)], 16-byte aligned
     float *wbuf = reinterpret_cast<float *>(rows + ((c.m * kRowWordsF32 + 3) & ~3));
     Zs[c.n + lane] = 0x7F800000u;   // dummy posterior +inf for unused edge slots
     if (use_bulk) {
@@ -244,7 +244,7 @@ static ldpc_status launch_learned_t(const Code &c, const float *d_llr, int64_t f
                                    const DecodeParams &p, uint32_t *d_hard, int32_t *d_iters,
                                    float *d_post, cudaStream_t s) {
     const int region_words = (posterior_words(c.n) + c.m * kRowWordsF32 + 3) & ~3;
-    const int smem = 16 + (region_words + 2 * c.mb * wpad(DMAX)) * 4;
+    const int smem = 16 + (region_words + kWeightBuffers * c.mb * wpad(DMAX)) * 4;
     int dev = 0, sms = 148, max_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

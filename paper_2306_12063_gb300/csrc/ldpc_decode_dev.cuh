@@ -652,11 +652,54 @@ __device__ __forceinline__ int64_t next_work(unsigned long long *ctr, int64_t ba
 }
 
 // ---------------------------------------------------------------------------
+// Learned weights in shared memory: three rows of mb * wpad(DMAX) floats in
+// slot order; iteration k reads row buffer k % 3 (weights of iteration k,
+// table row min(k, T) - 1) and, for the old messages, buffer (k - 1) % 3
+// (iteration 1 its own).  The row of iteration k + 1 is copied in
+// asynchronously while iteration k runs, into the buffer iteration k - 2
+// used; after iteration T + 2 all three buffers hold the last row and the
+// copies stop.
+// ---------------------------------------------------------------------------
+constexpr int kWeightBuffers = 3;
+
+// Issue the copies of iteration k's weights into buf (one commit group per
+// thread; unused slots get 0), threads tid = 0 .. nthr-1.
+template <int WP>
+__device__ __forceinline__ void stage_weights_async(const DevCode &c, const DecodeParams &p,
+                                                    int wT, int k, float *buf, int tid,
+                                                    int nthr) {
+    const float *wk = p.weights + static_cast<size_t>(min(k, wT) - 1) * p.n_edges;
+    for (int i = tid; i < c.mb * WP; i += nthr) {
+        const int g = __ldg(c.wgather + i);
+        if (g >= 0)
+            cp_async4(buf + i, wk + g);
+        else
+            buf[i] = 0.0f;
+    }
+    cp_async_commit();
+}
+
+// Before iteration k: issue iteration k + 1's weights when it needs a new
+// row, then wait for iteration k's (the caller synchronises the threads).
+template <int WP>
+__device__ __forceinline__ void weights_for_iteration(const DevCode &c, const DecodeParams &p,
+                                                      int wT, int k, float *wbuf, int tid,
+                                                      int nthr) {
+    const int j = k + 1;
+    if (j <= p.max_iters && j <= wT + 2) {
+        stage_weights_async<WP>(c, p, wT, j, wbuf + (j % kWeightBuffers) * c.mb * WP, tid, nthr);
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One FP32 frame: stage its LLRs (src, N words) into Zs, clear the messages,
 // run the layered iterations (eq. 22, 23, 20) with the syndrome stop after
 // each full iteration (eq. 21, Section 4 step 4).  Returns the iteration
 // count, or 0 if the bulk copy timed out (the status word records it).
-// Learned weights (WT) are staged per iteration into wbuf.
+// Learned weights (WT) stream into wbuf (kWeightBuffers rows) as above.
 // ---------------------------------------------------------------------------
 template <int DMAX, bool WT, int DM = DMAX>
 __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, uint32_t *rows,
@@ -669,27 +712,20 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
         for (int i = lane; i < c.n; i += 32) Zs[i] = __ldg(src + i);
     }
     for (int i = lane; i < c.m * kRowWordsF32; i += 32) rows[i] = 0u;   // all L_mn = 0
-    __syncwarp();
     const bool norm = p.normalise != 0;
     const int wT = p.weight_iters > 0 ? p.weight_iters : p.max_iters;
     const bool checkpoints = p.early_stop && (p.stop_iter[0] | p.stop_iter[1]) != 0;
     // give-up limits, floor(stop_frac * M) with the product rounded in FP32
     const int lim0 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[0], static_cast<float>(c.m))));
     const int lim1 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[1], static_cast<float>(c.m))));
+    constexpr int WP = wpad(DMAX);
+    if (WT) stage_weights_async<WP>(c, p, wT, 1, wbuf + c.mb * WP, lane, 32);
+    __syncwarp();
     for (int k = 1; k <= p.max_iters; ++k) {
-        constexpr int WP = wpad(DMAX);
-        float *wcur = wbuf + (k & 1) * c.mb * WP;
-        const float *wprev = k > 1 ? wbuf + ((k - 1) & 1) * c.mb * WP : wcur;
-        if (WT && k <= wT + 1) {
-            // stage the weights of iteration k (row min(k, T) - 1) in slot
-            // order; iteration 1 also serves as its own "previous" weights
-            // (they multiply zero messages).  From iteration T + 2 on both
-            // buffers already hold row T - 1.
-            const float *wk = p.weights + static_cast<size_t>(min(k, wT) - 1) * p.n_edges;
-            for (int i = lane; i < c.mb * WP; i += 32) {
-                const int g = __ldg(c.wgather + i);
-                wcur[i] = g >= 0 ? __ldg(wk + g) : 0.0f;
-            }
+        const float *wcur = wbuf + (k % kWeightBuffers) * c.mb * WP;
+        const float *wprev = k > 1 ? wbuf + ((k - 1) % kWeightBuffers) * c.mb * WP : wcur;
+        if (WT) {
+            weights_for_iteration<WP>(c, p, wT, k, wbuf, lane, 32);
             __syncwarp();
         }
         for (int l = 0; l < c.mb; ++l) {
@@ -697,13 +733,17 @@ __device__ __forceinline__ int decode_one_f32(const DevCode &c, uint32_t *Zs, ui
                                     wcur + l * WP);
             __syncwarp();
         }
+        bool stop = false;
         if (checkpoints && (k == p.stop_iter[0] || k == p.stop_iter[1])) {
             // a give-up checkpoint: count the unsatisfied checks; none ends
             // the frame (eq. 21), too many ends it too
             const int u = syndrome_count_f32<DMAX, DM>(c, Zs, lane);
-            if (u == 0 || (k == p.stop_iter[0] && u > lim0) || (k == p.stop_iter[1] && u > lim1))
-                return k;
-        } else if (p.early_stop && syndrome_ok_f32<DMAX, DM>(c, Zs, lane)) {
+            stop = u == 0 || (k == p.stop_iter[0] && u > lim0) || (k == p.stop_iter[1] && u > lim1);
+        } else if (p.early_stop) {
+            stop = syndrome_ok_f32<DMAX, DM>(c, Zs, lane);
+        }
+        if (stop) {
+            if (WT) cp_async_wait<0>();   // the next iteration's copies land before reuse
             return k;
         }
     }
@@ -777,22 +817,19 @@ __device__ __forceinline__ int decode_one_f32_team(const DevCode &c, uint32_t *Z
         for (int i = tid; i < c.n; i += nthr) Zs[i] = __ldg(src + i);
     }
     for (int i = tid; i < c.m * kRowWordsF32; i += nthr) rows[i] = 0u;   // all L_mn = 0
-    team_sync(bar_id, tstep);
     const bool norm = p.normalise != 0;
     const int wT = p.weight_iters > 0 ? p.weight_iters : p.max_iters;
     const bool checkpoints = p.early_stop && (p.stop_iter[0] | p.stop_iter[1]) != 0;
     const int lim0 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[0], static_cast<float>(c.m))));
     const int lim1 = static_cast<int>(floorf(__fmul_rn(p.stop_frac[1], static_cast<float>(c.m))));
+    constexpr int WP = wpad(DMAX);
+    if (WT) stage_weights_async<WP>(c, p, wT, 1, wbuf + c.mb * WP, tid, nthr);
+    team_sync(bar_id, tstep);
     for (int k = 1; k <= p.max_iters; ++k) {
-        constexpr int WP = wpad(DMAX);
-        float *wcur = wbuf + (k & 1) * c.mb * WP;
-        const float *wprev = k > 1 ? wbuf + ((k - 1) & 1) * c.mb * WP : wcur;
-        if (WT && k <= wT + 1) {
-            const float *wk = p.weights + static_cast<size_t>(min(k, wT) - 1) * p.n_edges;
-            for (int i = tid; i < c.mb * WP; i += nthr) {
-                const int g = __ldg(c.wgather + i);
-                wcur[i] = g >= 0 ? __ldg(wk + g) : 0.0f;
-            }
+        const float *wcur = wbuf + (k % kWeightBuffers) * c.mb * WP;
+        const float *wprev = k > 1 ? wbuf + ((k - 1) % kWeightBuffers) * c.mb * WP : wcur;
+        if (WT) {
+            weights_for_iteration<WP>(c, p, wT, k, wbuf, tid, nthr);
             team_sync(bar_id, tstep);
         }
         for (int l = 0; l < c.mb; ++l) {
@@ -808,8 +845,10 @@ __device__ __forceinline__ int decode_one_f32_team(const DevCode &c, uint32_t *Z
             int u = 0;
             for (int w = 0; w < tstep; ++w) u += tw[1 + w];
             if (u == 0 || (count && ((k == p.stop_iter[0] && u > lim0) ||
-                                     (k == p.stop_iter[1] && u > lim1))))
+                                     (k == p.stop_iter[1] && u > lim1)))) {
+                if (WT) cp_async_wait<0>();   // the next iteration's copies land before reuse
                 return k;
+            }
         }
     }
     return p.max_iters;

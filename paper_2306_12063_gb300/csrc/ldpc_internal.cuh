@@ -271,6 +271,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Asynchronous 4-byte copy global -> shared (no register staging); copies
+// issued since the last commit form one group, and wait_group<n> returns
+// once at most n of this thread's groups are still in flight.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Byte-wise mask from the top bit of each byte: 0xFF where bit 7 is set.
 __device__ __forceinline__ uint32_t msb_bytes_to_mask(uint32_t x) {
     uint32_t r;   // prmt selector nibble with bit 3 set replicates the byte's sign

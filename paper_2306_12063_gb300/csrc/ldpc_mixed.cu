@@ -37,7 +37,7 @@ namespace {
 
 // One FP32 launch: work items of the group's codes, one frame at a time.
 // WT: learned normalised min-sum with code c's weights wptr[c], a table of
-// wT[c] rows (staged per iteration after the row state); each code runs
+// wT[c] rows (streamed into buffers after the row state); each code runs
 // p.max_iters iterations when that is set, else wT[c], rows past the table
 // repeating its last one.
 template <int DMAX, bool WT = false>
@@ -452,7 +452,7 @@ struct MixedGroup {
     int dslots = 0;
     std::vector<int> codes;              // set indices, largest first
     int smem[2] = {0, 0};                // bytes per block: [0] FP32, [1] int8
-    int smem_learned = 0;                // FP32 plus two iterations of staged weights
+    int smem_learned = 0;                // FP32 plus the learned weight buffers
     int chunk[2] = {8, 16};              // frames per work item
     int per_sm[2] = {0, 0};              // resident blocks per SM (0: occupancy limit)
     int wpf = 1;                         // FP32 warps per frame (a team shares the rows)
@@ -826,8 +826,8 @@ ldpc_status ldpc_mixed_plan_create(const ldpc_codeset *set, const int32_t *h_cod
         MixedGroup &g = pl->groups.back();
         g.codes.push_back(ci);
         g.smem[0] = std::max(g.smem[0], region_bytes_f32(c));
-        g.smem_learned = std::max(g.smem_learned,
-                                  region_bytes_f32(c) + 8 * c.mb * ((c.dslots + 3) & ~3));
+        g.smem_learned = std::max(g.smem_learned, region_bytes_f32(c) + 4 * kWeightBuffers *
+                                                                           c.mb * wpad(c.dslots));
         g.smem[1] = std::max(g.smem[1], si8);
         if (c.n % 4) g.bulk_ok = false;
         if (!all_n4) g.bulk_ok = false;
