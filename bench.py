@@ -901,8 +901,8 @@ def profile_cases():
     2. mixed int8 and FP32 decoders (`mixed_i8_kernel`, `mixed_f32_kernel`) on
        the four R=3/4 WiMAX-shaped codes with Z = 84..96 (one launch group),
        65,536 frames;
-    3. Section 5 int16 wrap-around decoder (`decode_i16w_kernel`), N=1944,
-       65,536 frames at 4.0 dB;
+    3. Section 5 int16 wrap-around decoder (`decode_i16x2_kernel`, two frames
+       per word), N=1944, 65,536 frames at 4.0 dB;
     4. flooding FP32 decoder (`decode_flooding_kernel`), N=648, 16,384 frames,
        10 iterations;
     5. Alg. A1 bitmap encoder (`encode_bitmap_kernel`), N=2304 R=5/6, 262,144
