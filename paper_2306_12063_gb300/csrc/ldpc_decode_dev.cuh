@@ -69,13 +69,11 @@ __device__ __forceinline__ uint32_t lanes_even(uint32_t x) { return prmt(x, 0u, 
 __device__ __forceinline__ uint32_t lanes_odd(uint32_t x) { return prmt(x, 0u, 0x4341u); }
 __device__ __forceinline__ uint32_t lanes_even_sx(uint32_t x) { return prmt(x, 0u, 0xA280u); }
 __device__ __forceinline__ uint32_t lanes_odd_sx(uint32_t x) { return prmt(x, 0u, 0xB391u); }
-// min(max(a + b, 0), 254) on two signed 16-bit lanes (|a + b| < 32768):
-// the add and the max issue as one instruction.
+// min(max(a + b, 0), 254) on two signed 16-bit lanes (|a + b| < 32768),
+// as the add-min-relu intrinsic max(min(a + b, 254), 0) (the same value for
+// every input, since 0 <= 254).
 __device__ __forceinline__ uint32_t add_clamp_off16x2(uint32_t a, uint32_t b) {
-    const uint32_t r = __viaddmax_s16x2(a, b, 0u);
-    uint32_t o;
-    asm("min.s16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(0x00FE00FEu));
-    return o;
+    return __viaddmin_s16x2_relu(a, b, 0x00FE00FEu);
 }
 // 0xFF per byte where bit 7 of the low byte of a lane is set, lanes of e
 // holding frames 0, 2 and lanes of o frames 1, 3: back in frame-byte order.
