@@ -229,7 +229,9 @@ __device__ __forceinline__ void layer_i16x2(const DevCode &c, int layer, uint32_
             uint32_t g = bsel(bsel(G2, G1, nq), bsel(N2, N1, nq), sm);
             g = i < start ? 0u : g;
             const uint32_t q = wadd16x2(z, g);                 // eq. (22)
-            const uint32_t a = smax16x2(q, wneg16x2(q));       // |Z_mn| in 16 bits
+            // |Z_mn| in 16 bits: max(-q, q) with -q = ~q + 1 wrapped, the
+            // add and the max in one instruction
+            const uint32_t a = __viaddmax_s16x2(~q, 0x00010001u, q);
             Q[i] = q;
             A[i] = a;
             mn2 = smax16x2(mn1, smin16x2(mn2, a));
