@@ -181,10 +181,25 @@ __device__ __forceinline__ void layer_f32(const DevCode &c, int layer, int d, ui
             // learned weights: Z - w' m_old rounded once (fused)
             const float q = WT ? __fmaf_rn(-wp[WT ? i : 0], Lu, Q[i]) : __fsub_rn(Q[i], Lu);
             Q[i] = q;
-            const float a = fabsf(q);
+            sx ^= __float_as_uint(q);
+        }
+        // smallest and second smallest |Z_mn|, two slots at a time: the
+        // pair's min x and max y merge with (mn1, mn2) as mn1 = min(mn1, x),
+        // mn2 = min(max(mn1, x), mn2, y), the 3-way min on the bit patterns
+        // (non-negative floats order as unsigned integers)
+#pragma unroll
+        for (int i = 0; i + 1 < DMAX; i += 2) {
+            const float a = fabsf(Q[i]), b = fabsf(Q[i + 1]);
+            const float x = fminf(a, b), y = fmaxf(a, b);
+            const float hi = fmaxf(mn1, x);
+            mn1 = fminf(mn1, x);
+            mn2 = __uint_as_float(
+                __vimin3_u32(__float_as_uint(hi), __float_as_uint(mn2), __float_as_uint(y)));
+        }
+        if (DMAX & 1) {
+            const float a = fabsf(Q[DMAX - 1]);
             mn2 = fmaxf(mn1, fminf(mn2, a));
             mn1 = fminf(mn1, a);
-            sx ^= __float_as_uint(q);
         }
         const float n1 = (norm && !WT) ? __fmul_rn(alpha, mn1) : mn1;
         const float n2 = (norm && !WT) ? __fmul_rn(alpha, mn2) : mn2;
