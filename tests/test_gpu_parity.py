@@ -264,45 +264,53 @@ def test_dynamic_frame_handout(ldpc, request, dtype, shape_name, frames):
 
 @pytest.mark.parametrize("dtype", ["i8", "f32"])
 def test_full_size_wifi1944_sampled(ldpc, dtype):
-    """The 262,144-frame N=1944 batch at 4.0 dB, generated and decoded on
-    the GPU exactly as the benchmark does; a sample of frames is regenerated
-    and decoded independently by the oracle and must match bit for bit
-    (channel LLRs, hard decisions, iteration counts)."""
+    """The benchmark's step: the three 262,144-frame N=1944 batches (3.5, 4.0,
+    4.5 dB), generated on the GPU and decoded back to back by one call, as the
+    benchmark times them; a sample of frames from every batch (its first and
+    last frames among them) is regenerated and decoded independently by the
+    oracle and must match bit for bit (channel LLRs, hard decisions,
+    iteration counts)."""
     from paper_2306_12063_gb300.workload import make_batch
     s = SHAPES["wifi1944"]
     code = ldpc.Code(s.hbm, s.z)
     F = 262144
-    frame0 = F        # the second Eb/N0 batch of the benchmark
-    b = make_batch(code, F, frame0, 4.0)
+    ebn0 = (3.5, 4.0, 4.5)
+    batches = [make_batch(code, F, b * F, eb, keep_cw=False) for b, eb in enumerate(ebn0)]
     if dtype == "i8":
-        hard, iters, _ = code.decode(b.q, frames=F, dtype=ldpc.I8X4, max_iters=20,
+        x = torch.cat([b.q for b in batches])
+        hard, iters, _ = code.decode(x, frames=3 * F, dtype=ldpc.I8X4, max_iters=20,
                                      early_stop=True)
     else:
-        hard, iters, _ = code.decode(b.llr, dtype=ldpc.F32, max_iters=20, early_stop=True)
+        x = torch.cat([b.llr for b in batches])
+        hard, iters, _ = code.decode(x, dtype=ldpc.F32, max_iters=20, early_stop=True)
+    del x
     code.sync()
     rng = np.random.default_rng(99)
-    sample = np.unique(np.concatenate([[0, 1, 2, 3, F - 1], rng.integers(0, F, 40)]))
     rc = oracle.RefCode(s.hbm, s.z)
-    sig = synth.ebn0_db_to_sigma(4.0, rc.k / rc.n)
     h_np, i_np = to_np(hard).view(np.uint32), to_np(iters)
-    llr_gpu = to_np(b.llr[torch.from_numpy(sample).cuda()])
-    for row, f in enumerate(sample):
-        info = oracle.gen_info(1, frame0 + int(f), 1, rc.k)
-        cw = rc.encode(info)
-        llr = oracle.awgn_llr(cw, frame0 + int(f), 1, sig)
-        assert (llr.view(np.uint32) == llr_gpu[row].view(np.uint32)).all()
-        if dtype == "i8":
-            wh, wi, _, _ = rc.decode_layered_i8(oracle.quantize_i8(llr), 20, True, True,
-                                                want_post=False)
-        else:
-            wh, wi, _ = rc.decode_layered_f32(llr, 20, 0.75, True, True, want_post=False)
-        assert i_np[f] == wi[0], (f, i_np[f], wi[0])
-        assert (h_np[f] == wh[0]).all()
+    for bi, (b, eb) in enumerate(zip(batches, ebn0)):
+        sample = np.unique(np.concatenate([[0, 1, 2, 3, F - 1], rng.integers(0, F, 14)]))
+        sig = synth.ebn0_db_to_sigma(eb, rc.k / rc.n)
+        llr_gpu = to_np(b.llr[torch.from_numpy(sample).cuda()])
+        for row, f in enumerate(sample):
+            g = bi * F + int(f)   # frame identity and its row in the step's outputs
+            info = oracle.gen_info(1, g, 1, rc.k)
+            cw = rc.encode(info)
+            llr = oracle.awgn_llr(cw, g, 1, sig)
+            assert (llr.view(np.uint32) == llr_gpu[row].view(np.uint32)).all()
+            if dtype == "i8":
+                wh, wi, _, _ = rc.decode_layered_i8(oracle.quantize_i8(llr), 20, True, True,
+                                                    want_post=False)
+            else:
+                wh, wi, _ = rc.decode_layered_f32(llr, 20, 0.75, True, True, want_post=False)
+            assert i_np[g] == wi[0], (g, i_np[g], wi[0])
+            assert (h_np[g] == wh[0]).all()
     # properties that hold at any size
     assert i_np.min() >= 1 and i_np.max() <= 20
-    stats = to_np(code.frame_stats(b.info, hard, iters, 20))
+    info_all = torch.cat([b.info for b in batches])
+    stats = to_np(code.frame_stats(info_all, hard, iters, 20))
     assert stats[3] == i_np.sum()
-    assert stats[4:].sum() == F
+    assert stats[4:].sum() == 3 * F
 
 
 def test_frame_stats_match_numpy(ldpc):
