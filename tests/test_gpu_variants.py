@@ -66,6 +66,28 @@ def test_int16_wrap_decoder_bit_exact(ldpc, shape, ebn0, iters, norm, es):
     assert (gp.cpu().numpy() == wp).all()
 
 
+def test_int16_one_frame_kernel_on_a_code_too_large_to_pack(ldpc):
+    """A code whose packed two-frame row state (five words per check row)
+    exceeds the device's shared memory per block runs the one-frame-per-warp
+    int16 kernel (three words per row): mb = 31, nb = 32, Z = 384, the largest
+    shape the library takes.  Bit-exact against the oracle like the packed
+    kernel."""
+    shape = synth.random_small_code(9, 31, 32, 384)
+    n, m = 32 * 384, 31 * 384
+    limit = torch.cuda.get_device_properties(0).shared_memory_per_block_optin
+    assert 4 * (n + 32 + 5 * m) > limit >= 4 * (n + 32 + 3 * m)
+    rc, _, _, llr = _llr(shape, 9, 14.0)   # rate 1/32: frames stop after 2-5 iterations
+    q = oracle.quantize_i16(llr, 16.0, 10)
+    for es in (True, False):
+        wh, wi, wp, _ = rc.decode_layered_i16w(q, 6, normalise=True, early_stop=es)
+        code = ldpc.Code(shape.hbm, shape.z)
+        gh, gi, gp = code.decode(torch.from_numpy(q).cuda(), dtype=ldpc.I16W, max_iters=6,
+                                 normalise=True, early_stop=es, want_post=True)
+        assert (gi.cpu().numpy() == wi).all()
+        assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+        assert (gp.cpu().numpy() == wp).all()
+
+
 @pytest.mark.parametrize("shape,frames", [(synth.wifi_n648_r12(), 151),
                                           (synth.wifi_n1944_r56(), 77)])
 def test_int16_lane_refills(ldpc, request, shape, frames):
