@@ -331,7 +331,8 @@ def test_frame_stats_match_numpy(ldpc):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
-@pytest.mark.parametrize("frames,chunk", [(1000, 128), (30, 128), (33, 128), (151, 128), (17, 4)])
+@pytest.mark.parametrize("frames,chunk", [(1000, 128), (30, 128), (33, 128), (96, 128),
+                                          (97, 128), (151, 128), (17, 4)])
 def test_decode_host_pipeline(ldpc, dtype, frames, chunk):
     """End-to-end entry point on pinned host buffers equals the device call,
     with batches shorter than, equal to and just past the quarter-size first
