@@ -388,6 +388,16 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
         graph_ms = time_fn(lambda: g.launch())
         st = reduce_counters(cnt.cpu().numpy())
 
+        def same_contents_direct():
+            # the graph's contents launched one by one on the stream
+            if dt == ldpc.I8X4:
+                plan.quantize(batch.llr, out=qg)
+            plan.decode(qg if dt == ldpc.I8X4 else batch.llr, dt, max_iters=MAX_ITERS,
+                        out=(hard, iters, None))
+            plan.stats(batch.info, hard, iters, MAX_ITERS)
+
+        same_ms = time_fn(same_contents_direct)
+
         def per_code_step():
             for code, llr_c, q_c, n_c in per_code:
                 if dt == ldpc.I8X4:
@@ -409,7 +419,10 @@ def mixed_leg(args, ldpc, torch, dev, stream, barrier, rank, ws, pg):
                      "graph_step": {"value": info_bits * ws / (graph_ms * 1e-3) / 1e9,
                                     "ms": graph_ms,
                                     "contents": ("quantise + " if dt == ldpc.I8X4 else "")
-                                    + f"{plan.n_groups} decode launches + error counting"},
+                                    + f"{plan.n_groups} decode launches + error counting",
+                                    "same_contents_direct": {
+                                        "value": info_bits * ws / (same_ms * 1e-3) / 1e9,
+                                        "ms": same_ms}},
                      "per_code_launches": {"value": info_bits * ws / (pc_ms * 1e-3) / 1e9,
                                            "ms": pc_ms, "launches": len(per_code)},
                      "alg_tops": ops / (direct_ms * 1e-3) / 1e12,
