@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(32)
             const uint32_t sel = (0x3210u & ~(0xFu << (4 * b))) |
                                  (static_cast<uint32_t>(4 + (nf & 3)) << (4 * b));
             __syncwarp();
+            // eight loads in flight per lane (sixteen cost more than they hide)
+#pragma unroll 8
             for (int i = lane; i < c.n; i += 32)
                 Zs[i] = prmt(Zs[i], to_offset127(__ldg(src + i)), sel);
             const uint32_t keep = ~(0xFFu << (8 * b));
