@@ -1193,21 +1193,28 @@ def main():
 
         for _ in range(args.warmup):
             e2e_step()
-        barrier()
         a = torch.cuda.Event(enable_timing=True)
         b_ = torch.cuda.Event(enable_timing=True)
         e_steps = max(1, args.steps // 2)
-        a.record(stream)
-        for _ in range(e_steps):
-            e2e_step()
-        b_.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        e_ms = a.elapsed_time(b_)
-        if pg is not None:
-            tt = torch.tensor([e_ms], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        # three timed windows of e_steps steps each; the line reports the
+        # median window (the host link is shared with the machine's other
+        # GPUs, and a transient there can slow one window) and all three
+        windows = []
+        for _ in range(3):
+            barrier()
+            a.record(stream)
+            for _ in range(e_steps):
+                e2e_step()
+            b_.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            w_ms = a.elapsed_time(b_)
+            if pg is not None:
+                tt = torch.tensor([w_ms], device=dev)
+                pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+                w_ms = float(tt.item())
+            windows.append(w_ms)
+        e_ms = statistics.median(windows)
         # the box's pinned host-to-device copy rate, beside the number: the
         # host link is shared with the machine's other GPUs
         probe = host_q[0].view(-1)[: (256 << 20) // 4]
@@ -1221,6 +1228,8 @@ def main():
         h2d_gbs = 3 * probe.numel() * 4 / (a.elapsed_time(b_) * 1e-3) / 1e9
         del probe_d
         e2e = {"value": bits_per_step * e_steps / (e_ms * 1e-3) / 1e9, "unit": "Gbit/s",
+               "windows": [bits_per_step * e_steps / (w * 1e-3) / 1e9 for w in windows],
+               "statistic": f"median of 3 timed windows of {e_steps} steps",
                "h2d_copy_gbs": h2d_gbs,
                "h2d_bytes_per_step": sum(int(h.numel()) * 4 for h in host_q),
                "d2h_bytes_per_step": sum(int(h.numel()) * 4 for h in h_hard) +
