@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(32 * kTrainWarps)
     if (f >= frames) return;   // the whole warp leaves together
     const int n = c.n, z = c.z, m = c.m, E = c.n_edges;
     float *Zs = smem + warp * zstride;
+#pragma unroll 8
     for (int i = lane; i < n; i += 32) Zs[i] = llr[f * n + i];
     __syncwarp();
     double acc = 0.0;
@@ -177,6 +178,8 @@ __global__ void __launch_bounds__(32 * kTrainWarps)
         const float *pt = post + (static_cast<size_t>(t - 1) * frames + f) * n;
         const float *zin = t >= 2 ? post + (static_cast<size_t>(t - 2) * frames + f) * n
                                   : llr + f * n;
+        // the loads of eight positions in flight per lane
+#pragma unroll 8
         for (int i = lane; i < n; i += 32) {
             const float p1 = 1.0f / (1.0f + expf(pt[i]));
             gZ[i] += loss_scale * (static_cast<float>(cb[i] & 1u) - p1);
@@ -262,13 +265,25 @@ __global__ void __launch_bounds__(32 * kTrainWarps)
                 }
             }
             __syncwarp();
-            // weight gradient of this layer: sum of the row terms per block edge
+            // weight gradient of this layer: sum of the row terms per block
+            // edge, the d warp reductions interleaved (independent shuffles)
             float *gw = gw_frame + (static_cast<size_t>(f) * T + (t - 1)) * E;
-            for (int i = 0; i < d; ++i) {
-                float s = 0.0f;
-                for (int r = lane; r < z; r += 32) s += Qs[(e0 + i) * z + r];
-                s = warp_sum(s);
-                if (lane == 0) gw[e0 + i] = s;
+            float s[DMAX];
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i) {
+                s[i] = 0.0f;
+                if (i < d)
+                    for (int r = lane; r < z; r += 32) s[i] += Qs[(e0 + i) * z + r];
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < DMAX; ++i) s[i] += __shfl_xor_sync(0xFFFFFFFFu, s[i], o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < DMAX; ++i)
+                    if (i < d) gw[e0 + i] = s[i];
             }
         }
         __syncwarp();
