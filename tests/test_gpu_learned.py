@@ -55,6 +55,24 @@ def test_learned_bit_exact(ldpc, shape, T, ebn0, frames):
     assert (gp.cpu().numpy() == wp).all()
 
 
+@pytest.mark.parametrize("T,iters", [(1, 1), (1, 3), (2, 1), (3, 2), (2, 4), (5, 5)])
+def test_learned_short_runs_bit_exact(ldpc, T, iters):
+    """Runs of one to five iterations and tables of one to five rows: the
+    weight rows streamed in ahead of each iteration (and the last row reused
+    past the table) equal the oracle's decoder, with and without early stop."""
+    shape = synth.wifi_n648_r12()
+    rc, _, llr = _inputs(shape, 96, 2.5, frame0=7)
+    w = _weights(rc, T, 23)
+    code = ldpc.Code(shape.hbm, shape.z)
+    for es in (False, True):
+        wh, wi, wp = rc.decode_learned_f32(llr, w, max_iters=iters, early_stop=es)
+        gh, gi, gp = code.decode_learned(torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda(),
+                                         max_iters=iters, early_stop=es, want_post=True)
+        assert (gi.cpu().numpy() == wi).all()
+        assert (gh.cpu().numpy().view(np.uint32) == wh).all()
+        assert (gp.cpu().numpy() == wp).all()
+
+
 def test_learned_negative_and_mixed_weights(ldpc):
     """Weights of either sign (the sign multiplies the message sign)."""
     shape = synth.wifi_n648_r12()
