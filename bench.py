@@ -914,7 +914,10 @@ def profile_cases():
     (``python bench.py --profile-cases``):
 
     1. learned FP32 decoder (`decode_f32_kernel<8, true>`), N=648, 65,536 frames,
-       T = 8, weights 0.8, Eb/N0 uniform in [1.5, 4.5) dB;
+       T = 8, weights 0.8, Eb/N0 uniform in [1.5, 4.5) dB, a fixed 8
+       iterations; then the plain FP32 decoder (`decode_f32_kernel<8, false>`)
+       on the same frames, also a fixed 8 iterations (the two launches' counts
+       compare per frame-iteration);
     2. mixed int8 and FP32 decoders (`mixed_i8_kernel`, `mixed_f32_kernel`) on
        the four R=3/4 WiMAX-shaped codes with Z = 84..96 (one launch group),
        65,536 frames;
@@ -951,7 +954,8 @@ def profile_cases():
     llr648 = awgn_llr_frames(cw, 0, 1, sig)
     w = torch.full((8, c648.nnz_blocks), 0.8, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    c648.decode_learned(llr648, w, early_stop=True)
+    c648.decode_learned(llr648, w, early_stop=False)
+    c648.decode(llr648, max_iters=8, early_stop=False)
     torch.cuda.synchronize()
     # 2. mixed batch, one launch group
     shapes = [s for s in synth.wimax_mixed_set() if s.mb == 6 and s.z >= 84]
